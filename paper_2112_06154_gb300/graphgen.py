@@ -1,0 +1,245 @@
+"""Seeded synthetic graph generators (inputs only).
+
+Every generator returns a simple undirected graph as a symmetric CSR pair
+``(rowptr int64[n+1], col int32[2m])`` with each row sorted ascending, no
+self-loops and no duplicate edges.  This module holds none of the (k,h)-core
+method's arithmetic: it only draws edges.  Both the CUDA path and the CPU
+oracle read graphs made here, so the two never share anything else.
+
+Workload shapes (stand-ins for the paper's SNAP/KONECT graphs, which are not
+available offline):
+
+* ``erdos_renyi(n, m)``: G(n, m), m distinct uniform edges.
+* ``chung_lu(n, avg_deg, gamma, max_deg)``: power-law expected degrees
+  w_i proportional to (i + i0)^(-1/(gamma-1)), scaled to ``avg_deg`` and capped at
+  ``max_deg``; edges drawn with endpoints proportional to w, self-loops and
+  duplicates dropped.
+* ``rmat(scale, edge_factor, a, b, c)``: recursive-matrix edges, symmetrised,
+  deduplicated, self-loops dropped, vertex ids permuted by a seeded permutation.
+* ``barabasi_albert(n, m)``: preferential attachment (copy model), deduplicated.
+* ``grid(a, b, shortcut_frac)``: a x b lattice plus random shortcut edges.
+* closed-form graphs: complete, path, cycle, star, grid.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "csr_from_edges", "erdos_renyi", "chung_lu", "rmat", "barabasi_albert",
+    "grid", "complete", "path", "cycle", "star", "random_small",
+    "pack_batch", "graph_stats",
+]
+
+
+def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray):
+    """Symmetric, sorted, deduplicated CSR from an undirected edge list."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    lo = np.minimum(u, v)
+    hi = np.maximum(u, v)
+    key = np.unique(lo * n + hi)
+    lo = key // n
+    hi = key - lo * n
+    src = np.concatenate([lo, hi])
+    dst = np.concatenate([hi, lo])
+    order = np.lexsort((dst, src))
+    src = src[order]
+    dst = dst[order]
+    counts = np.bincount(src, minlength=n).astype(np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return rowptr, dst.astype(np.int32)
+
+
+def erdos_renyi(n: int, m: int, seed: int):
+    """G(n, m): ``m`` distinct edges drawn uniformly without replacement."""
+    rng = np.random.default_rng(seed)
+    total = n * (n - 1) // 2
+    if m > total:
+        raise ValueError("m exceeds the number of vertex pairs")
+    chosen = np.empty(0, dtype=np.int64)
+    while chosen.size < m:
+        need = m - chosen.size
+        draw = rng.integers(0, total, size=int(need * 1.2) + 16, dtype=np.int64)
+        chosen = np.unique(np.concatenate([chosen, draw]))
+    chosen = rng.permutation(chosen)[:m]
+    # decode pair index -> (i, j), i < j, row-major over the upper triangle
+    i = (n - 2 - np.floor(np.sqrt(-8.0 * chosen + 4.0 * n * (n - 1) - 7) / 2.0 - 0.5)).astype(np.int64)
+    j = chosen + i + 1 - n * (n - 1) // 2 + (n - i) * ((n - i) - 1) // 2
+    return csr_from_edges(n, i, j)
+
+
+def chung_lu(n: int, avg_deg: float, gamma: float, max_deg: int, seed: int):
+    """Chung-Lu power-law graph with expected degrees w_i (see module doc)."""
+    rng = np.random.default_rng(seed)
+    idx = np.arange(n, dtype=np.float64)
+    w = (idx + 10.0) ** (-1.0 / (gamma - 1.0))
+    w = np.minimum(w * (avg_deg * n / w.sum()), max_deg)
+    w *= avg_deg * n / w.sum()
+    w = np.minimum(w, max_deg)
+    m_draw = int(round(w.sum() / 2.0))
+    p = w / w.sum()
+    cdf = np.cumsum(p)
+    cdf[-1] = 1.0
+    u = np.searchsorted(cdf, rng.random(m_draw), side="right")
+    v = np.searchsorted(cdf, rng.random(m_draw), side="right")
+    np.minimum(u, n - 1, out=u)
+    np.minimum(v, n - 1, out=v)
+    perm = rng.permutation(n)
+    return csr_from_edges(n, perm[u], perm[v])
+
+
+def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int):
+    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale edge draws."""
+    rng = np.random.default_rng(seed)
+    n = 1 << scale
+    m_draw = edge_factor * n
+    u = np.zeros(m_draw, dtype=np.int64)
+    v = np.zeros(m_draw, dtype=np.int64)
+    ab = a + b
+    abc = a + b + c
+    chunk = 1 << 24
+    for s in range(0, m_draw, chunk):
+        e = min(m_draw, s + chunk)
+        uu = np.zeros(e - s, dtype=np.int64)
+        vv = np.zeros(e - s, dtype=np.int64)
+        for lvl in range(scale):
+            x = rng.random(e - s)
+            bit = np.int64(1) << np.int64(scale - 1 - lvl)
+            down = x >= ab                      # quadrants c, d: row bit set
+            right = ((x >= a) & (x < ab)) | (x >= abc)  # quadrants b, d: column bit set
+            uu |= np.where(down, bit, 0)
+            vv |= np.where(right, bit, 0)
+        u[s:e] = uu
+        v[s:e] = vv
+    perm = rng.permutation(n).astype(np.int64)
+    return csr_from_edges(n, perm[u], perm[v])
+
+
+def barabasi_albert(n: int, m: int, seed: int):
+    """Preferential attachment via the copy model.
+
+    Vertex t >= m attaches ``m`` edges; each edge endpoint is a uniformly drawn
+    entry of the endpoint list of all earlier edges (or a uniform earlier
+    vertex for the seed clique), which selects targets with probability
+    proportional to degree.  Duplicate targets collapse (dedup), so a vertex
+    may end with fewer than ``m`` edges.
+    """
+    rng = np.random.default_rng(seed)
+    if n <= m + 1:
+        return complete(n)
+    # seed: clique on vertices 0..m
+    cu, cv = np.triu_indices(m + 1, k=1)
+    n0 = cu.size
+    t = np.arange(m + 1, n, dtype=np.int64)
+    ne = (n - m - 1) * m
+    src = np.repeat(t, m)
+    # endpoint list: entries 2e, 2e+1 for edge e (seed edges first); a new
+    # vertex draws among the endpoints of all edges created before it
+    first_e_of_src = n0 + (src - (m + 1)) * m
+    limit = 2 * first_e_of_src
+    pick = (rng.random(ne) * limit).astype(np.int64)
+    ends_u = np.concatenate([cu.astype(np.int64), src])
+    # resolve picks by pointer jumping: even position -> source of the edge,
+    # odd position -> target of the edge (which may itself be a pick)
+    tgt = np.empty(n0 + ne, dtype=np.int64)
+    tgt[:n0] = cv
+    ptr = np.full(n0 + ne, -1, dtype=np.int64)
+    is_odd = (pick & 1) == 1
+    eid = pick >> 1
+    direct = ~is_odd
+    tgt_new = np.where(direct, ends_u[eid], -1)
+    seed_ref = is_odd & (eid < n0)
+    tgt_new = np.where(seed_ref, cv[np.minimum(eid, n0 - 1)], tgt_new)
+    ptr_new = np.where(is_odd & (eid >= n0), eid, -1)
+    tgt[n0:] = tgt_new
+    ptr[n0:] = ptr_new
+    for _ in range(64):
+        pend = ptr >= 0
+        if not pend.any():
+            break
+        idx = np.nonzero(pend)[0]
+        p = ptr[idx]
+        nxt = ptr[p]
+        resolved = nxt < 0
+        new_tgt = tgt[p]
+        tgt[idx[resolved]] = new_tgt[resolved]
+        ptr[idx] = nxt
+    return csr_from_edges(n, ends_u, tgt)
+
+
+def grid(a: int, b: int, shortcut_frac: float = 0.0, seed: int = 0):
+    """a x b 4-neighbour lattice, plus round(shortcut_frac * m) random edges."""
+    idx = np.arange(a * b, dtype=np.int64).reshape(a, b)
+    u = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    v = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    k = int(round(shortcut_frac * u.size))
+    if k > 0:
+        rng = np.random.default_rng(seed)
+        su = rng.integers(0, a * b, size=k)
+        sv = rng.integers(0, a * b, size=k)
+        u = np.concatenate([u, su])
+        v = np.concatenate([v, sv])
+    return csr_from_edges(a * b, u, v)
+
+
+def complete(n: int):
+    u, v = np.triu_indices(n, k=1)
+    return csr_from_edges(n, u, v)
+
+
+def path(n: int):
+    u = np.arange(n - 1)
+    return csr_from_edges(n, u, u + 1)
+
+
+def cycle(n: int):
+    u = np.arange(n)
+    return csr_from_edges(n, u, (u + 1) % n)
+
+
+def star(leaves: int):
+    return csr_from_edges(leaves + 1, np.zeros(leaves, dtype=np.int64), np.arange(1, leaves + 1))
+
+
+def random_small(n: int, p: float, seed: int):
+    """G(n, p) for tiny brute-force cases."""
+    rng = np.random.default_rng(seed)
+    u, v = np.triu_indices(n, k=1)
+    keep = rng.random(u.size) < p
+    return csr_from_edges(n, u[keep], v[keep])
+
+
+def pack_batch(graphs):
+    """Pack graphs into one offset-indexed CSR.
+
+    Returns ``(vtx_off int64[g+1], rowptr int64[N+1], col int32[...])`` where
+    graph ``i`` owns vertices ``vtx_off[i] .. vtx_off[i+1]-1`` and its column
+    indices are global (shifted by ``vtx_off[i]``).
+    """
+    sizes = [int(rp.size - 1) for rp, _ in graphs]
+    vtx_off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=vtx_off[1:])
+    rps = []
+    cols = []
+    base_e = 0
+    for i, (rp, cl) in enumerate(graphs):
+        rps.append(rp[:-1] + base_e)
+        cols.append(cl.astype(np.int64) + vtx_off[i])
+        base_e += int(rp[-1])
+    rowptr = np.concatenate(rps + [np.array([base_e], dtype=np.int64)]).astype(np.int64)
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    return vtx_off, rowptr, col
+
+
+def graph_stats(rowptr, col):
+    deg = np.diff(rowptr)
+    return {
+        "n": int(rowptr.size - 1),
+        "m": int(col.size // 2),
+        "max_deg": int(deg.max()) if deg.size else 0,
+        "sum_deg2": int((deg.astype(np.int64) ** 2).sum()),
+        "isolated": int((deg == 0).sum()),
+    }
