@@ -1,0 +1,134 @@
+/*
+ * khcore.h -- C ABI of the GB300 (sm_103a) library for distance-generalized
+ * (k,h)-cores, after Tatti, "Fast computation of distance-generalized cores
+ * using sampling".
+ *
+ * Terms (paper, Sec. 2-3):
+ *   N(v; h, X)   nodes reachable from v by a path of at most h edges inside the
+ *                alive node set X; deg_h(v; X) = |N(v; h, X)| - 1.
+ *   (k,h)-core   maximal node set whose members all have deg_h >= k inside it;
+ *                the core number c(v) is the largest such k containing v.
+ *   r[v]         geometric(1/2) rank, P(r >= j) = 2^-j (Sec. 3, Alg. 4).
+ *   M            sample budget of Eq. (buffer).
+ *   B[v,i],k[v,i]  nodes of N(v; i) with rank >= k[v,i], k[v,i] the smallest
+ *                level leaving at most M of them (Sec. 3, Prop. 3.1).
+ *   estimate     Alg. 1 / Def. 4.1: |B[v,h] \ {v}| 2^k, raised to M 2^(k-1)
+ *                when k > 0.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative KH_E* code.  No call aborts, exits or
+ *     traps; the text of the last error of a context is kh_last_error().
+ *   - Graphs are simple and undirected, given as a symmetric CSR with int64
+ *     row offsets and int32 column indices, each row strictly increasing, no
+ *     self-loops.  Node ids must be below 2^27 (sampled lists pack the rank in
+ *     the top 5 bits of a 32-bit key).
+ *   - Output arrays are caller-allocated.  Without KH_DEVICE_PTR they are host
+ *     memory and the call returns after the results are written.  With
+ *     KH_DEVICE_PTR they are device memory of the context's device and the
+ *     call only enqueues work on the context's stream (kh_sync waits).
+ *   - Every result is a deterministic function of (graph, h, seed, M).
+ *   - A context and its graphs must be used from one host thread at a time.
+ */
+#ifndef KHCORE_H
+#define KHCORE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KH_OK 0
+#define KH_EINVAL (-1)    /* bad argument (null pointer, h < 1, M < 1, ...) */
+#define KH_EGRAPH (-2)    /* CSR not simple/symmetric/sorted, or ids >= 2^27 */
+#define KH_ENOMEM (-3)    /* device or host allocation failed */
+#define KH_ECUDA (-4)     /* a CUDA runtime call failed */
+#define KH_ETIMEOUT (-5)  /* a bounded device loop gave up (peel round limit) */
+#define KH_EINTERNAL (-6) /* a device-side bounds check fired */
+
+#define KH_DEVICE_PTR 1u  /* pointer arguments are device memory */
+
+typedef struct kh_ctx kh_ctx;
+typedef struct kh_graph kh_graph;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on, or NULL for a stream the library creates and owns.
+ * *out receives the context; destroy it with kh_ctx_destroy. */
+int kh_ctx_create(kh_ctx **out, int device, void *cuda_stream);
+int kh_ctx_destroy(kh_ctx *ctx);
+
+/* Text of the last error reported by a call on `ctx` (never NULL). */
+const char *kh_last_error(kh_ctx *ctx);
+
+/* Load a graph (Sec. 2: G = (V, E), n nodes, undirected).  rowptr has n+1
+ * int64 entries, col has rowptr[n] int32 entries.  The library copies both
+ * into device memory it owns; the caller keeps ownership of its arrays.
+ * flags & KH_DEVICE_PTR: rowptr/col are device pointers.  The graph is
+ * validated on the device: KH_EGRAPH if a row is unsorted or has duplicates,
+ * a column is out of range or a self-loop, or an edge lacks its reverse. */
+int kh_graph_load_csr(kh_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *col,
+                      uint32_t flags, kh_graph **out);
+int kh_graph_free(kh_graph *g);
+
+/* Number of nodes of a loaded graph. */
+int kh_graph_n(kh_graph *g, int64_t *n);
+
+/* Path length h >= 1 of h-neighbourhoods (Sec. 2; h = 1 gives ordinary
+ * k-cores).  Default 2. */
+int kh_set_h(kh_graph *g, int32_t h);
+
+/* Sampling parameters (Sec. 3).  seed: SplitMix64 seed of the ranks r[v]
+ * (r[v] = trailing zeros of the v-th output, capped at 31).  M_or_0 > 0 sets
+ * M directly; M_or_0 == 0 sets M = floor(1 + 4(2+eps)/eps^2 (log(2n/delta) +
+ * log 8)) (Eq. (buffer), natural log).  Requires eps > 0, 0 < delta < 1 when
+ * M_or_0 == 0; M must lie in [1, 16000].  Default: seed 1, eps 0.5,
+ * delta 0.05. */
+int kh_set_sampling(kh_graph *g, uint64_t seed, int64_t M_or_0, double eps, double delta);
+
+/* The budget M in force. */
+int kh_get_M(kh_graph *g, int64_t *M);
+
+/* Ranks r[v], uint8[n] (Sec. 3; Alg. 4 first loop). */
+int kh_ranks(kh_graph *g, uint8_t *r, uint32_t flags);
+
+/* Exact h-degrees of the whole graph, deg[v] = |N(v; h, V)| - 1, int32[n]
+ * (Sec. 2). */
+int kh_hdegree_exact(kh_graph *g, int32_t *deg, uint32_t flags);
+
+/* Fixed-level sampled counts of the whole graph: cnt[v*(j_hi-j_lo+1) +
+ * (j-j_lo)] = |{u in N(v; h, V), u != v : r[u] >= j}|, int32, for
+ * 0 <= j_lo <= j_hi <= 31.  cnt * 2^j is Alg. 1's estimate with the level
+ * forced to j, i.e. sampling probability 2^-j; j = 0 gives deg_h. */
+int kh_sampled_counts(kh_graph *g, int32_t j_lo, int32_t j_hi, int32_t *cnt, uint32_t flags);
+
+/* Adaptive estimate of the whole graph (Alg. 1 after the level recursion
+ * of Prop. 3.1 / Alg. 2): est uint64[n], level = k[v,h] uint8[n] (may be
+ * NULL), bsize = |B[v,h]| int32[n] (may be NULL). */
+int kh_estimate(kh_graph *g, uint64_t *est, uint8_t *level, int32_t *bsize, uint32_t flags);
+
+/* ExactCore (Sec. 2): core[v] = c(v), int32[n], by bucket-synchronous peeling
+ * (c = max(c, min deg_h); every alive v with deg_h <= c is removed at once),
+ * which equals one-at-a-time peeling because deg_h never grows as nodes
+ * leave.  After each round the h-ball of the removed nodes is recomputed. */
+int kh_core_exact(kh_graph *g, int32_t *core, uint32_t flags);
+
+/* Core (Alg. 4) with the estimate in place of deg_h: core[v] = c'(v),
+ * uint64[n], bucket-synchronous as above (the estimate never grows as nodes
+ * leave, Prop. 4.2); the lists are refreshed level by level where their
+ * inputs changed (Alg. 3). */
+int kh_core_sampled(kh_graph *g, uint64_t *core, uint32_t flags);
+
+/* Statistics of the last kh_core_* call: round_of[v] (int32[n], may be NULL)
+ * is the peeling round that removed v; *rounds the number of rounds;
+ * *updates the number of node (re)computations including the initial pass.
+ * Host pointers only. */
+int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updates);
+
+/* Wait for all work enqueued on the graph's context stream. */
+int kh_sync(kh_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KHCORE_H */

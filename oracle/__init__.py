@@ -66,6 +66,10 @@ def _load():
     lib.kho_core_exact.restype = i64
     lib.kho_core_sampled.argtypes = [i64, P, P, P, i32, i64, u32, P, P]
     lib.kho_core_sampled.restype = i64
+    lib.kho_hdegree_some.argtypes = [i64, P, P, P, i32, P, i64, P]
+    lib.kho_hdegree_some.restype = ctypes.c_int
+    lib.kho_estimate_def_some.argtypes = [i64, P, P, P, P, i32, i64, P, i64, P, P, P]
+    lib.kho_estimate_def_some.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -182,3 +186,28 @@ def core_sampled(rowptr, col, r, h: int, M: int, mode: int = 0):
     steps = _load().kho_core_sampled(n, _p(rowptr), _p(col), _p(r), h, M, mode, _p(core), _p(rnd))
     _check(steps, "core_sampled")
     return core[:n], rnd[:n], int(steps)
+
+
+def hdegree_some(rowptr, col, h: int, vertices, alive=None) -> np.ndarray:
+    """deg_h(v; X) for the listed nodes only."""
+    rowptr, col, n = _graph(rowptr, col)
+    vs = np.ascontiguousarray(vertices, dtype=np.int32)
+    deg = np.zeros(max(vs.size, 1), dtype=np.int32)
+    _check(_load().kho_hdegree_some(n, _p(rowptr), _p(col), _p(_alive(alive, n)), h, _p(vs),
+                                    vs.size, _p(deg)), "hdegree_some")
+    return deg[:vs.size]
+
+
+def estimate_def_some(rowptr, col, r, h: int, M: int, vertices, alive=None):
+    """Def. 4.1 (est, k, bsize) for the listed nodes only."""
+    rowptr, col, n = _graph(rowptr, col)
+    r = np.ascontiguousarray(r, dtype=np.uint8)
+    vs = np.ascontiguousarray(vertices, dtype=np.int32)
+    m = max(vs.size, 1)
+    est = np.zeros(m, dtype=np.uint64)
+    k = np.zeros(m, dtype=np.uint8)
+    bs = np.zeros(m, dtype=np.int32)
+    _check(_load().kho_estimate_def_some(n, _p(rowptr), _p(col), _p(_alive(alive, n)), _p(r), h, M,
+                                         _p(vs), vs.size, _p(est), _p(k), _p(bs)),
+           "estimate_def_some")
+    return est[:vs.size], k[:vs.size], bs[:vs.size]

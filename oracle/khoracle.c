@@ -774,3 +774,69 @@ out:
     free(W.mark);
     return steps;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Per-node versions for sampled checks on large graphs                      */
+/* ------------------------------------------------------------------------ */
+
+/* deg_h(v; X) for the nodes listed in vs[0..count). */
+int kho_hdegree_some(int64_t n, const int64_t *rowptr, const int32_t *col,
+                     const uint8_t *alive, int32_t h, const int32_t *vs, int64_t count,
+                     int32_t *deg)
+{
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!buf || !dist) {
+        free(buf);
+        free(dist);
+        return KHO_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; i++)
+        dist[i] = -1;
+    for (int64_t q = 0; q < count; q++) {
+        int64_t s = kho_hball(n, rowptr, col, alive, vs[q], h, buf, dist);
+        deg[q] = s > 0 ? (int32_t)(s - 1) : 0;
+    }
+    free(buf);
+    free(dist);
+    return KHO_OK;
+}
+
+/* Def. 4.1 estimate for the nodes listed in vs[0..count). */
+int kho_estimate_def_some(int64_t n, const int64_t *rowptr, const int32_t *col,
+                          const uint8_t *alive, const uint8_t *r, int32_t h, int64_t M,
+                          const int32_t *vs, int64_t count,
+                          uint64_t *est, uint8_t *kap, int32_t *bsize)
+{
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    uint8_t *x = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!buf || !dist || !x || M < 1) {
+        free(buf);
+        free(dist);
+        free(x);
+        return M < 1 ? KHO_EINVAL : KHO_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; i++)
+        dist[i] = -1;
+    for (int64_t q = 0; q < count; q++) {
+        uint8_t k = 0;
+        int32_t s = 0;
+        uint64_t e = 0;
+        int64_t d = kho_hball(n, rowptr, col, alive, vs[q], h, buf, dist);
+        if (d > 0) {
+            for (int64_t j = 0; j < d; j++)
+                x[j] = r[buf[j]];
+            e = def41(x, d, M, &k, &s);
+        }
+        est[q] = e;
+        if (kap)
+            kap[q] = k;
+        if (bsize)
+            bsize[q] = s;
+    }
+    free(buf);
+    free(dist);
+    free(x);
+    return KHO_OK;
+}

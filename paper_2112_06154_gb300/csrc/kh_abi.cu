@@ -1,0 +1,455 @@
+// kh_abi.cu -- the extern "C" entry points declared in include/khcore.h:
+// contexts, graph loading and validation, parameters, and the calls that run
+// the exact and sampled paths.  Every device array of a graph is allocated
+// here once and reused across calls.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "kh_internal.cuh"
+
+namespace kh {
+
+int set_error(kh_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int check_cuda(kh_ctx* ctx, cudaError_t e, const char* what) {
+    const int code = (e == cudaErrorMemoryAllocation) ? KH_ENOMEM : KH_ECUDA;
+    cudaGetLastError();  // clear a sticky-free error so the context stays usable
+    return set_error(ctx, code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <typename T>
+static int dalloc(kh_ctx* ctx, T** p, size_t count, const char* what) {
+    if (*p) return KH_OK;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return check_cuda(ctx, e, what);
+    }
+    return KH_OK;
+}
+
+template <typename T>
+static void dfree(T** p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+int ensure_work(Graph& g) {
+    const size_t n = (size_t)g.n;
+    int rc;
+    if ((rc = dalloc(g.ctx, &g.alive, n, "alive"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.d32, n, "d32"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.d64, n, "d64"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.core32, n, "core32"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.core64, n, "core64"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.round_of, n, "round_of"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.seen, n, "seen"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listR, n, "listR"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listA, n, "listA"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listB, n, "listB"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listW, n, "listW"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listC[0], n, "listC0"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listC[1], n, "listC1"))) return rc;
+    return KH_OK;
+}
+
+int ensure_lists(Graph& g) {
+    // lists for levels 1..h-1, sizes/levels for 1..h
+    const int64_t need_keys = (int64_t)(g.h - 1) * g.n * g.cap;
+    if (g.keys && g.keys_levels * g.n * g.cap < need_keys) dfree(&g.keys);
+    if (g.lsz && g.lvl_alloc < g.h) {
+        dfree(&g.lsz);
+        dfree(&g.lk);
+    }
+    int rc;
+    if (need_keys > 0) {
+        if ((rc = dalloc(g.ctx, &g.keys, (size_t)need_keys, "sample lists"))) return rc;
+        g.keys_levels = g.h - 1;
+    }
+    if (!g.lsz) g.lvl_alloc = g.h;
+    if ((rc = dalloc(g.ctx, &g.lsz, (size_t)g.lvl_alloc * g.n, "list sizes"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.lk, (size_t)g.lvl_alloc * g.n, "list levels"))) return rc;
+    if (!g.ranks_valid) {
+        launch_ranks(g, g.ctx->stream);
+        g.ranks_valid = true;
+    }
+    return KH_OK;
+}
+
+int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps) {
+    if (g.queues && g.scratch_ctas >= ctas && (!bitmaps || g.gbitmaps)) return KH_OK;
+    // enlarging: wait for in-flight users of the old scratch first
+    if (g.queues || g.gbitmaps) {
+        cudaError_t e = cudaStreamSynchronize(g.ctx->stream);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "sync before scratch resize");
+    }
+    dfree(&g.queues);
+    dfree(&g.gbitmaps);
+    int rc;
+    if ((rc = dalloc(g.ctx, &g.queues, (size_t)ctas * (size_t)g.n, "BFS queues"))) return rc;
+    if (bitmaps) {
+        const size_t words = (size_t)((g.n + 31) / 32);
+        if ((rc = dalloc(g.ctx, &g.gbitmaps, (size_t)ctas * words, "BFS bitmaps"))) return rc;
+    }
+    g.scratch_ctas = ctas;
+    return KH_OK;
+}
+
+static int64_t budget_M(int64_t n, double eps, double delta) {
+    // Eq. (buffer): M = 1 + 4(2 + eps)/eps^2 (C + log 8), C = log(2n/delta)
+    const double C = std::log(2.0 * (double)n / delta);
+    return (int64_t)std::floor(1.0 + 4.0 * (2.0 + eps) / (eps * eps) * (C + std::log(8.0)));
+}
+
+static void free_graph_arrays(Graph& g) {
+    dfree(&g.rowptr);
+    dfree(&g.col);
+    dfree(&g.rank);
+    dfree(&g.alive);
+    dfree(&g.keys);
+    dfree(&g.lsz);
+    dfree(&g.lk);
+    dfree(&g.d32);
+    dfree(&g.d64);
+    dfree(&g.core32);
+    dfree(&g.core64);
+    dfree(&g.round_of);
+    dfree(&g.seen);
+    dfree(&g.listR);
+    dfree(&g.listA);
+    dfree(&g.listB);
+    dfree(&g.listW);
+    dfree(&g.listC[0]);
+    dfree(&g.listC[1]);
+    dfree(&g.state);
+    dfree(&g.queues);
+    dfree(&g.gbitmaps);
+}
+
+static int set_M(Graph& g, int64_t M) {
+    if (M < 1 || M > kMaxM)
+        return set_error(g.ctx, KH_EINVAL, "M = %lld outside [1, %d]", (long long)M, kMaxM);
+    if (M != g.M) {
+        g.M = M;
+        const int64_t cap = (M + 3) & ~(int64_t)3;
+        if (cap > g.cap) dfree(&g.keys);
+        if (cap > g.cap) g.cap = cap;
+    }
+    return KH_OK;
+}
+
+static int copy_out(Graph& g, void* dst, const void* src, size_t bytes, uint32_t flags) {
+    cudaStream_t s = g.ctx->stream;
+    if (bytes == 0) return KH_OK;
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(dst, src, bytes,
+                                       (flags & KH_DEVICE_PTR) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyDeviceToHost, s));
+    if (!(flags & KH_DEVICE_PTR)) KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
+    return KH_OK;
+}
+
+static int finish_check(Graph& g) {
+    int err = 0;
+    cudaStream_t s = g.ctx->stream;
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&err, &g.state->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
+    if (err) return set_error(g.ctx, KH_EINTERNAL, "device check failed (flags 0x%x)", err);
+    return KH_OK;
+}
+
+}  // namespace kh
+
+using kh::Graph;
+
+extern "C" {
+
+int kh_ctx_create(kh_ctx** out, int device, void* cuda_stream) {
+    if (!out) return KH_EINVAL;
+    *out = nullptr;
+    kh_ctx* c = (kh_ctx*)calloc(1, sizeof(kh_ctx));
+    if (!c) return KH_ENOMEM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            c->stream = (cudaStream_t)cuda_stream;
+            c->own_stream = false;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e != cudaSuccess) {
+        free(c);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? KH_ENOMEM : KH_ECUDA;
+    }
+    *out = c;
+    return KH_OK;
+}
+
+int kh_ctx_destroy(kh_ctx* ctx) {
+    if (!ctx) return KH_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    free(ctx);
+    return KH_OK;
+}
+
+const char* kh_last_error(kh_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->err;
+}
+
+int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
+                      uint32_t flags, kh_graph** out) {
+    if (!ctx || !out) return KH_EINVAL;
+    *out = nullptr;
+    if (n < 0 || (n > 0 && (!rowptr))) return kh::set_error(ctx, KH_EINVAL, "bad n or rowptr");
+    if (n > (int64_t)kh::kIdMask)
+        return kh::set_error(ctx, KH_EGRAPH, "n = %lld exceeds 2^27 - 1 node ids", (long long)n);
+    cudaError_t ce = cudaSetDevice(ctx->device);
+    if (ce != cudaSuccess) return kh::check_cuda(ctx, ce, "cudaSetDevice");
+    const bool dev = (flags & KH_DEVICE_PTR) != 0;
+    cudaStream_t s = ctx->stream;
+    int64_t ends[2] = {0, 0};
+    if (n > 0) {
+        if (dev) {
+            ce = cudaMemcpyAsync(&ends[0], rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(&ends[1], rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) return kh::check_cuda(ctx, ce, "read rowptr ends");
+        } else {
+            ends[0] = rowptr[0];
+            ends[1] = rowptr[n];
+        }
+    }
+    const int64_t nnz = ends[1];
+    if (ends[0] != 0 || nnz < 0 || nnz > ((int64_t)1 << 40))
+        return kh::set_error(ctx, KH_EGRAPH, "rowptr must start at 0 and end at nnz >= 0");
+    if (nnz > 0 && !col) return kh::set_error(ctx, KH_EINVAL, "null col");
+    kh_graph* G = (kh_graph*)calloc(1, sizeof(kh_graph));
+    if (!G) return KH_ENOMEM;
+    Graph& g = G->g;
+    g.ctx = ctx;
+    g.n = n;
+    g.nnz = nnz;
+    g.h = 2;
+    g.seed = 1;
+    g.M = 0;
+    g.cap = 0;
+    int rc = KH_OK;
+    if ((rc = kh::dalloc(ctx, &g.rowptr, (size_t)n + 1, "rowptr")) ||
+        (rc = kh::dalloc(ctx, &g.col, (size_t)nnz, "col")) ||
+        (rc = kh::dalloc(ctx, &g.rank, (size_t)n, "rank")) ||
+        (rc = kh::dalloc(ctx, &g.state, 1, "state"))) {
+        kh::free_graph_arrays(g);
+        free(G);
+        return rc;
+    }
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ce = cudaMemcpyAsync(g.rowptr, rowptr, sizeof(int64_t) * (size_t)(n + 1), kind, s);
+    if (ce == cudaSuccess && nnz > 0)
+        ce = cudaMemcpyAsync(g.col, col, sizeof(int32_t) * (size_t)nnz, kind, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g.state, 0, sizeof(kh::DevState), s);
+    if (ce != cudaSuccess) {
+        rc = kh::check_cuda(ctx, ce, "copy CSR");
+        kh::free_graph_arrays(g);
+        free(G);
+        return rc;
+    }
+    // row offsets must be nondecreasing: checked by the validation kernel
+    // (a decreasing pair is flagged there), together with sorted rows,
+    // in-range ids, no self-loops and symmetry
+    kh::launch_validate(g, &g.state->err, s);
+    int err = 0;
+    ce = cudaMemcpyAsync(&err, &g.state->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        rc = kh::check_cuda(ctx, ce, "validate CSR");
+        kh::free_graph_arrays(g);
+        free(G);
+        return rc;
+    }
+    if (err) {
+        kh::free_graph_arrays(g);
+        free(G);
+        return kh::set_error(ctx, KH_EGRAPH,
+                             "graph is not a simple symmetric CSR with sorted rows");
+    }
+    rc = kh::set_M(g, kh::budget_M(n > 0 ? n : 1, 0.5, 0.05));
+    if (rc) {
+        kh::free_graph_arrays(g);
+        free(G);
+        return rc;
+    }
+    *out = G;
+    return KH_OK;
+}
+
+int kh_graph_free(kh_graph* G) {
+    if (!G) return KH_EINVAL;
+    cudaSetDevice(G->g.ctx->device);
+    cudaStreamSynchronize(G->g.ctx->stream);
+    kh::free_graph_arrays(G->g);
+    free(G);
+    return KH_OK;
+}
+
+int kh_graph_n(kh_graph* G, int64_t* n) {
+    if (!G || !n) return KH_EINVAL;
+    *n = G->g.n;
+    return KH_OK;
+}
+
+int kh_set_h(kh_graph* G, int32_t h) {
+    if (!G) return KH_EINVAL;
+    if (h < 1 || h > kh::kMaxH) return kh::set_error(G->g.ctx, KH_EINVAL, "h = %d outside [1, %d]", h, kh::kMaxH);
+    G->g.h = h;
+    return KH_OK;
+}
+
+int kh_set_sampling(kh_graph* G, uint64_t seed, int64_t M_or_0, double eps, double delta) {
+    if (!G) return KH_EINVAL;
+    Graph& g = G->g;
+    int64_t M = M_or_0;
+    if (M_or_0 < 0) return kh::set_error(g.ctx, KH_EINVAL, "M must be >= 0");
+    if (M_or_0 == 0) {
+        if (!(eps > 0.0) || !(delta > 0.0) || !(delta < 1.0) || !std::isfinite(eps))
+            return kh::set_error(g.ctx, KH_EINVAL, "need eps > 0 and 0 < delta < 1");
+        M = kh::budget_M(g.n > 0 ? g.n : 1, eps, delta);
+    }
+    int rc = kh::set_M(g, M);
+    if (rc) return rc;
+    if (seed != g.seed) {
+        g.seed = seed;
+        g.ranks_valid = false;
+    }
+    return KH_OK;
+}
+
+int kh_get_M(kh_graph* G, int64_t* M) {
+    if (!G || !M) return KH_EINVAL;
+    *M = G->g.M;
+    return KH_OK;
+}
+
+int kh_ranks(kh_graph* G, uint8_t* r, uint32_t flags) {
+    if (!G || (!r && G->g.n > 0)) return KH_EINVAL;
+    Graph& g = G->g;
+    cudaSetDevice(g.ctx->device);
+    if (!g.ranks_valid) {
+        kh::launch_ranks(g, g.ctx->stream);
+        g.ranks_valid = true;
+    }
+    KH_CUDA_TRY(g.ctx, cudaGetLastError());
+    return kh::copy_out(g, r, g.rank, (size_t)g.n, flags);
+}
+
+int kh_hdegree_exact(kh_graph* G, int32_t* deg, uint32_t flags) {
+    if (!G || (!deg && G->g.n > 0)) return KH_EINVAL;
+    Graph& g = G->g;
+    cudaSetDevice(g.ctx->device);
+    cudaStream_t s = g.ctx->stream;
+    int rc = kh::ensure_work(g);
+    if (rc) return rc;
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
+    rc = kh::launch_hdeg(g, nullptr, nullptr, g.n, g.d32, nullptr, 0, 0, s);
+    if (rc) return rc;
+    KH_CUDA_TRY(g.ctx, cudaGetLastError());
+    rc = kh::copy_out(g, deg, g.d32, sizeof(int32_t) * (size_t)g.n, flags);
+    if (rc) return rc;
+    return (flags & KH_DEVICE_PTR) ? KH_OK : kh::finish_check(g);
+}
+
+int kh_sampled_counts(kh_graph* G, int32_t j_lo, int32_t j_hi, int32_t* cnt, uint32_t flags) {
+    if (!G || (!cnt && G->g.n > 0)) return KH_EINVAL;
+    Graph& g = G->g;
+    if (j_lo < 0 || j_hi > 31 || j_lo > j_hi)
+        return kh::set_error(g.ctx, KH_EINVAL, "need 0 <= j_lo <= j_hi <= 31");
+    cudaSetDevice(g.ctx->device);
+    cudaStream_t s = g.ctx->stream;
+    int rc = kh::ensure_work(g);
+    if (rc) return rc;
+    if (!g.ranks_valid) {
+        kh::launch_ranks(g, s);
+        g.ranks_valid = true;
+    }
+    const int nj = j_hi - j_lo + 1;
+    int32_t* dcnt = nullptr;
+    if (flags & KH_DEVICE_PTR) {
+        dcnt = cnt;
+    } else if (g.n > 0) {
+        KH_CUDA_TRY(g.ctx, cudaMallocAsync((void**)&dcnt, sizeof(int32_t) * (size_t)g.n * nj, s));
+    }
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
+    rc = kh::launch_hdeg(g, nullptr, nullptr, g.n, g.d32, dcnt, j_lo, nj, s);
+    if (rc == KH_OK && !(flags & KH_DEVICE_PTR) && g.n > 0) {
+        rc = kh::copy_out(g, cnt, dcnt, sizeof(int32_t) * (size_t)g.n * nj, 0);
+    }
+    if (dcnt && !(flags & KH_DEVICE_PTR)) cudaFreeAsync(dcnt, s);
+    if (rc) return rc;
+    KH_CUDA_TRY(g.ctx, cudaGetLastError());
+    return (flags & KH_DEVICE_PTR) ? KH_OK : kh::finish_check(g);
+}
+
+int kh_estimate(kh_graph* G, uint64_t* est, uint8_t* level, int32_t* bsize, uint32_t flags) {
+    if (!G || (!est && G->g.n > 0)) return KH_EINVAL;
+    Graph& g = G->g;
+    cudaSetDevice(g.ctx->device);
+    int rc = kh::run_estimate_all(g);
+    if (rc) return rc;
+    const size_t off = (size_t)(g.h - 1) * (size_t)g.n;
+    rc = kh::copy_out(g, est, g.d64, sizeof(uint64_t) * (size_t)g.n, flags);
+    if (!rc && level) rc = kh::copy_out(g, level, g.lk + off, (size_t)g.n, flags);
+    if (!rc && bsize) rc = kh::copy_out(g, bsize, g.lsz + off, sizeof(int32_t) * (size_t)g.n, flags);
+    return rc;
+}
+
+int kh_core_exact(kh_graph* G, int32_t* core, uint32_t flags) {
+    if (!G || (!core && G->g.n > 0)) return KH_EINVAL;
+    cudaSetDevice(G->g.ctx->device);
+    return kh::run_core(G->g, false, core, nullptr, (flags & KH_DEVICE_PTR) != 0);
+}
+
+int kh_core_sampled(kh_graph* G, uint64_t* core, uint32_t flags) {
+    if (!G || (!core && G->g.n > 0)) return KH_EINVAL;
+    cudaSetDevice(G->g.ctx->device);
+    return kh::run_core(G->g, true, core, nullptr, (flags & KH_DEVICE_PTR) != 0);
+}
+
+int kh_peel_info(kh_graph* G, int32_t* round_of, int64_t* rounds, int64_t* updates) {
+    if (!G) return KH_EINVAL;
+    Graph& g = G->g;
+    if (!g.have_rounds) return kh::set_error(g.ctx, KH_EINVAL, "no peeling has run on this graph");
+    if (rounds) *rounds = g.last_rounds;
+    if (updates) *updates = g.last_updates;
+    if (round_of && g.n > 0) {
+        cudaSetDevice(g.ctx->device);
+        return kh::copy_out(g, round_of, g.round_of, sizeof(int32_t) * (size_t)g.n, 0);
+    }
+    return KH_OK;
+}
+
+int kh_sync(kh_graph* G) {
+    if (!G) return KH_EINVAL;
+    cudaSetDevice(G->g.ctx->device);
+    KH_CUDA_TRY(G->g.ctx, cudaStreamSynchronize(G->g.ctx->stream));
+    return KH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,373 @@
+// kh_exact.cu -- ranks, CSR validation, exact h-degrees, removed-set balls.
+//
+// Exact h-degree (Sec. 2): deg_h(v; X) = |N(v; h, X)| - 1, N taken inside the
+// alive set X.  One CTA runs one bounded breadth-first search at a time and
+// takes the next source from a global counter (dynamic scheduling over a
+// persistent grid).  The visited set is a bitmap of n bits, in shared memory
+// when it fits (cleared with vector stores between sources) or else in a
+// per-CTA global scratch slice (cleared by walking the visit queue).  Each
+// frontier is expanded warp-per-vertex; vertices of degree >= kHeavyDeg (and a
+// lone frontier vertex) are expanded by the whole CTA.  New vertices are
+// appended to the CTA's queue with one warp-aggregated atomic per warp step.
+#include <cstdio>
+
+#include "kh_internal.cuh"
+
+namespace kh {
+
+namespace {
+
+constexpr int kBfsThreads = 256;
+constexpr int kHeavyDeg = 128;
+constexpr int kMaxHeavy = 64;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// SplitMix64 output function (Steele, Lea, Flood 2014).  The u-th output of a
+// generator seeded with s is mix(s + (u + 1) * golden), so each rank is
+// computed independently from its counter.
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_ranks(uint8_t* __restrict__ r, int64_t n, uint64_t seed) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const uint64_t x = splitmix_mix(seed + (uint64_t)(u + 1) * 0x9E3779B97F4A7C15ull);
+        // trailing zeros, capped at 31: geometric(1/2) rank of Sec. 3
+        r[u] = (uint8_t)(__ffsll((long long)(x | (1ull << 31))) - 1);
+    }
+}
+
+// One warp per row: rows strictly increasing, ids in range, no self-loops,
+// and every edge (u, v) has its reverse (binary search in row v).
+__global__ void k_validate(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           int64_t n, int64_t nnz, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        const int64_t b = rowptr[u], e = rowptr[u + 1];
+        if (b < 0 || e < b || e > nnz) {
+            if (lane == 0) atomicOr(err, kErrGraph);
+            continue;
+        }
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t v = col[k];
+            bool bad = v < 0 || (int64_t)v >= n || v == (int32_t)u;
+            if (!bad && k > b && col[k - 1] >= v) bad = true;
+            int64_t lo = 0, hi = -1;
+            if (!bad) {
+                lo = rowptr[v];
+                hi = rowptr[v + 1] - 1;
+                if (lo < 0 || hi >= nnz || hi < lo - 1) bad = true;
+            }
+            if (!bad) {
+                bool found = false;
+                while (lo <= hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    const int32_t x = col[mid];
+                    if (x == (int32_t)u) { found = true; break; }
+                    if (x < (int32_t)u) lo = mid + 1; else hi = mid - 1;
+                }
+                bad = !found;
+            }
+            if (bad) atomicOr(err, kErrGraph);
+        }
+    }
+}
+
+struct BfsArgs {
+    const int64_t* rowptr;
+    const int32_t* col;
+    const uint8_t* alive;
+    const uint8_t* rank;
+    int64_t n;
+    int h;
+    int words;                 // bitmap words
+    const int32_t* worklist;   // nullptr: sources 0..count_static-1
+    const int* d_count;
+    int64_t count_static;
+    int32_t* deg;
+    int32_t* cnt;              // fixed-level counts (RANKS only)
+    int jlo, nj;
+    int32_t* queues;           // per-CTA queue, qcap entries each
+    int64_t qcap;
+    uint32_t* gbitmaps;        // per-CTA bitmaps (global mode)
+    int* work_ctr;
+    int* err;
+    unsigned long long* updates;
+};
+
+// Visit neighbour u of a frontier vertex (all 32 lanes call this together;
+// `valid` false for lanes past the end of the row).
+template <bool RANKS>
+__device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
+                                      int* s_hist, bool valid, int32_t u, bool push, int lane,
+                                      int& my) {
+    bool isnew = false;
+    if (valid && a.alive[u] == 1) {
+        const uint32_t bit = 1u << (u & 31);
+        uint32_t* wp = bm + (u >> 5);
+        if (!(*(volatile uint32_t*)wp & bit)) {
+            const uint32_t old = atomicOr(wp, bit);
+            isnew = !(old & bit);
+        }
+    }
+    if (isnew) {
+        ++my;
+        if (RANKS) atomicAdd(&s_hist[a.rank[u]], 1);
+    }
+    if (push) {
+        const uint32_t nm = __ballot_sync(kFull, isnew);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(s_qtail, __popc(nm));
+            base = __shfl_sync(kFull, base, leader);
+            if (isnew) {
+                const int pos = base + __popc(nm & ((1u << lane) - 1u));
+                if (pos < a.qcap) q[pos] = u;
+                else atomicOr(a.err, kErrQueue);
+            }
+        }
+    }
+}
+
+template <bool RANKS, bool SMEM>
+__global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
+    extern __shared__ __align__(16) uint32_t s_bm_dyn[];
+    __shared__ int s_src, s_qtail, s_count, s_nheavy;
+    __shared__ int s_hist[32];
+    __shared__ int s_heavy[kMaxHeavy];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    uint32_t* bm = SMEM ? s_bm_dyn : a.gbitmaps + (size_t)blockIdx.x * (size_t)a.words;
+    int32_t* q = a.queues + (size_t)blockIdx.x * (size_t)a.qcap;
+    const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+
+    for (int i = tid; i < a.words; i += blockDim.x) bm[i] = 0u;
+    __syncthreads();
+
+    for (;;) {
+        if (tid == 0) s_src = atomicAdd(a.work_ctr, 1);
+        __syncthreads();
+        const int64_t idx = s_src;
+        if (idx >= total) break;
+        const int v = a.worklist ? a.worklist[idx] : (int)idx;
+        if (a.alive[v] != 1) {
+            if (tid == 0) a.deg[v] = 0;
+            if (RANKS && tid < a.nj) a.cnt[(size_t)v * a.nj + tid] = 0;
+            __syncthreads();
+            continue;
+        }
+        if (tid == 0) {
+            q[0] = v;
+            s_qtail = 1;
+            s_count = 0;
+            bm[v >> 5] |= 1u << (v & 31);
+        }
+        if (RANKS && tid < 32) s_hist[tid] = 0;
+        __syncthreads();
+        int fs = 0, fe = 1, my = 0;
+        for (int d = 0; d < a.h; ++d) {
+            // vertices found at distance d+1 are queued if they will be expanded,
+            // or, in global-bitmap mode, so the bitmap can be cleared by a walk
+            const bool push = (d + 1 < a.h) || !SMEM;
+            if (tid == 0) s_nheavy = 0;
+            __syncthreads();
+            const bool single = (fe - fs) == 1;
+            for (int i = fs + warp; i < fe; i += nwarps) {
+                const int w = q[i];
+                const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
+                if (single || e - b >= kHeavyDeg) {
+                    int slot = 0;
+                    if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
+                    slot = __shfl_sync(kFull, slot, 0);
+                    if (slot < kMaxHeavy) {
+                        if (lane == 0) s_heavy[slot] = w;
+                        continue;
+                    }
+                }
+                for (int64_t k0 = b; k0 < e; k0 += 32) {
+                    const int64_t k = k0 + lane;
+                    const bool valid = k < e;
+                    const int32_t u = valid ? a.col[k] : 0;
+                    visit<RANKS>(a, bm, q, &s_qtail, s_hist, valid, u, push, lane, my);
+                }
+            }
+            __syncthreads();
+            const int nh = min(s_nheavy, kMaxHeavy);
+            for (int hi = 0; hi < nh; ++hi) {
+                const int w = s_heavy[hi];
+                const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
+                for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
+                    const int64_t k = k0 + lane;
+                    const bool valid = k < e;
+                    const int32_t u = valid ? a.col[k] : 0;
+                    visit<RANKS>(a, bm, q, &s_qtail, s_hist, valid, u, push, lane, my);
+                }
+            }
+            __syncthreads();
+            fs = fe;
+            fe = min(s_qtail, (int)a.qcap);
+            if (fs >= fe) break;  // nothing new: the ball is complete
+        }
+        // reduce the count of newly visited vertices
+        for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(kFull, my, off);
+        if (lane == 0 && my) atomicAdd(&s_count, my);
+        __syncthreads();
+        if (tid == 0) {
+            a.deg[v] = s_count;
+            atomicAdd(a.updates, 1ull);
+        }
+        if (RANKS && tid < a.nj) {
+            int c = 0;
+            for (int j = a.jlo + tid; j < 32; ++j) c += s_hist[j];
+            a.cnt[(size_t)v * a.nj + tid] = c;
+        }
+        // clear the visited set for the next source
+        if (SMEM) {
+            uint4* b4 = reinterpret_cast<uint4*>(bm);
+            const int w4 = a.words >> 2;
+            for (int i = tid; i < w4; i += blockDim.x) b4[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (int i = (w4 << 2) + tid; i < a.words; i += blockDim.x) bm[i] = 0u;
+        } else {
+            const int qt = min(s_qtail, (int)a.qcap);
+            for (int i = tid; i < qt; i += blockDim.x) bm[q[i] >> 5] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// One hop of the ball around the removed set R in the OLD graph (alive != 0):
+// every newly reached vertex joins the next frontier (if more hops follow) and,
+// when it is still alive (alive == 1), the recompute work list.
+__global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
+                           const int32_t* __restrict__ fin, const int* __restrict__ nfin,
+                           int32_t* __restrict__ fout, int* nfout, int32_t* __restrict__ wl, int* nwl,
+                           const DevState* __restrict__ st, int push_next, int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const int nin = *nfin;
+    const int stamp = st->round * kPhaseStride;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
+        const int w = fin[i];
+        const int64_t b = rowptr[w], e = rowptr[w + 1];
+        for (int64_t k0 = b; k0 < e; k0 += 32) {
+            const int64_t k = k0 + lane;
+            bool isnew = false;
+            int32_t u = 0;
+            if (k < e) {
+                u = col[k];
+                if (alive[u] != 0 && *(volatile int32_t*)(seen + u) != stamp)
+                    isnew = atomicExch(seen + u, stamp) != stamp;
+            }
+            const bool to_f = isnew && push_next;
+            const bool to_w = isnew && alive[u] == 1;
+            uint32_t m1 = __ballot_sync(kFull, to_f);
+            uint32_t m2 = __ballot_sync(kFull, to_w);
+            int b1 = 0, b2 = 0;
+            if (lane == 0) {
+                if (m1) b1 = atomicAdd(nfout, __popc(m1));
+                if (m2) b2 = atomicAdd(nwl, __popc(m2));
+            }
+            b1 = __shfl_sync(kFull, b1, 0);
+            b2 = __shfl_sync(kFull, b2, 0);
+            const uint32_t lower = (1u << lane) - 1u;
+            if (to_f) {
+                const int p = b1 + __popc(m1 & lower);
+                if (p < cap) fout[p] = u;
+            }
+            if (to_w) {
+                const int p = b2 + __popc(m2 & lower);
+                if (p < cap) wl[p] = u;
+            }
+        }
+    }
+}
+
+int pick_grid(int sm, int per_sm, int64_t work) {
+    int64_t g = (int64_t)sm * per_sm;
+    if (work < g) g = work;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void launch_ranks(const Graph& g, cudaStream_t s) {
+    if (g.n == 0) return;
+    const int grid = pick_grid(g.ctx->sm_count, 4, (g.n + 255) / 256);
+    k_ranks<<<grid, 256, 0, s>>>(g.rank, g.n, g.seed);
+}
+
+void launch_validate(const Graph& g, int* d_err, cudaStream_t s) {
+    if (g.n == 0) return;
+    const int grid = pick_grid(g.ctx->sm_count, 8, (g.n * 32 + 255) / 256);
+    k_validate<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.n, g.nnz, d_err);
+}
+
+int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
+                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s) {
+    if (g.n == 0) return KH_OK;
+    if (!worklist && count_static == 0) return KH_OK;
+    const int words = (int)((g.n + 31) / 32);
+    const int64_t words_padded = ((int64_t)words + 3) & ~(int64_t)3;
+    const bool smem = words_padded * 4 <= kSmemBitmapMax;
+    const size_t dyn = smem ? (size_t)words_padded * 4 : 0;
+    void (*kern)(BfsArgs);
+    if (cnt) kern = smem ? k_hdeg<true, true> : k_hdeg<true, false>;
+    else kern = smem ? k_hdeg<false, true> : k_hdeg<false, false>;
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_hdeg)");
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBfsThreads, dyn);
+    if (e != cudaSuccess) return check_cuda(g.ctx, e, "occupancy(k_hdeg)");
+    if (per_sm < 1) per_sm = 1;
+    if (!smem && per_sm > 2) per_sm = 2;  // global bitmaps: bound the scratch
+    int64_t work = worklist ? g.n : count_static;
+    const int grid = pick_grid(g.ctx->sm_count, per_sm, work);
+    int rc = ensure_bfs_scratch(g, grid, !smem);
+    if (rc) return rc;
+    BfsArgs a;
+    a.rowptr = g.rowptr;
+    a.col = g.col;
+    a.alive = g.alive;
+    a.rank = g.rank;
+    a.n = g.n;
+    a.h = g.h;
+    a.words = words;
+    a.worklist = worklist;
+    a.d_count = d_count;
+    a.count_static = count_static;
+    a.deg = deg;
+    a.cnt = cnt;
+    a.jlo = jlo;
+    a.nj = nj;
+    a.queues = g.queues;
+    a.qcap = g.n;
+    a.gbitmaps = g.gbitmaps;
+    a.work_ctr = &g.state->work_ctr[0];
+    a.err = &g.state->err;
+    a.updates = &g.state->updates;
+    e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
+    if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    kern<<<grid, kBfsThreads, dyn, s>>>(a);
+    return KH_OK;
+}
+
+void launch_ball_hop(Graph& g, int hop, cudaStream_t s) {
+    // hop 1 starts from R; hop k >= 2 from the frontier written by hop k-1
+    const int32_t* fin = hop == 1 ? g.listR : (hop & 1 ? g.listB : g.listA);
+    const int* nfin = hop == 1 ? &g.state->nR : &g.state->nF[(hop - 1) & 1];
+    int32_t* fout = hop & 1 ? g.listA : g.listB;
+    int* nfout = &g.state->nF[hop & 1];
+    cudaMemsetAsync(nfout, 0, sizeof(int), s);
+    const int grid = g.ctx->sm_count * 8;
+    k_ball_hop<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, fin, nfin, fout, nfout,
+                                    g.listW, &g.state->nW, g.state, hop < g.h ? 1 : 0, g.n);
+}
+
+}  // namespace kh

@@ -1,0 +1,155 @@
+// kh_internal.cuh -- internal declarations of the (k,h)-core CUDA library.
+//
+// Device data layout of one graph (all arrays in HBM, owned by kh_graph):
+//   rowptr   int64[n+1], col int32[nnz]      symmetric CSR, rows sorted
+//   rank     uint8[n]                          r[v] (Sec. 3)
+//   alive    uint8[n]                          1 alive, 2 removed in the current
+//                                              peeling round (still part of the
+//                                              old graph), 0 removed earlier
+//   keys     uint32[(h-1) * n * cap]           B[v,i] for levels i = 1..h-1, one
+//                                              fixed slot of cap >= M keys per
+//                                              (level, node); key = r << 27 | id,
+//                                              grouped by rank, highest first
+//   lsz      int32[h * n], lk uint8[h * n]     |B[v,i]| and k[v,i], i = 1..h
+//   d32 / d64                                  deg_h (exact) or estimate (sampled)
+//   seen     int32[n]                          stamp array for frontier dedup
+//   lists    int32[n] x 4                      removed set, frontiers, work lists
+//   state    kh_dev_state                      round counters (device resident)
+//   scratch  per-CTA BFS queues (and bitmaps when n is too large for shared memory)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/khcore.h"
+
+namespace kh {
+
+constexpr int kRankBits = 5;
+constexpr int kIdBits = 27;
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
+constexpr int kMaxM = 16000;
+constexpr int kMaxH = 16;
+constexpr int kPhaseStride = 32;  // stamp = round * kPhaseStride + phase
+// Shared-memory visited bitmap limit per CTA (bytes); larger n uses global scratch.
+constexpr int64_t kSmemBitmapMax = 100 * 1024;
+
+// Error bits written by device-side checks.
+constexpr int kErrQueue = 1;   // BFS queue overflow
+constexpr int kErrProbe = 2;   // hash probe limit reached
+constexpr int kErrList = 4;    // list larger than its slot
+constexpr int kErrGraph = 8;   // CSR validation failure
+
+struct DevState {
+    unsigned long long c;        // current core value (max of round minima)
+    unsigned long long minval;   // min d over alive nodes in this round
+    int round;                   // current round index
+    int n_alive;                 // alive nodes at the start of the round
+    int n_alive_next;            // alive nodes after this round's removal
+    int nR;                      // |R| removed this round
+    int nF[2];                   // frontier sizes (exact refresh)
+    int nW;                      // work-list size
+    int nC[2];                   // changed-list sizes (sampled refresh, ping-pong)
+    int work_ctr[4];             // dynamic scheduling counters
+    unsigned long long updates;  // node recomputations
+    int err;                     // kErr* bits
+    int pad;
+};
+
+struct Graph;
+
+// ---- launchers (kh_exact.cu) -------------------------------------------------
+void launch_ranks(const Graph& g, cudaStream_t s);
+void launch_validate(const Graph& g, int* d_err, cudaStream_t s);
+// exact h-degrees of `count` nodes (worklist == nullptr: nodes 0..n-1) into deg32;
+// when cnt != nullptr also the fixed-level counts for j in [jlo, jlo+nj).
+int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
+                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s);
+// one hop of the removed set's ball in the old graph (exact refresh)
+void launch_ball_hop(Graph& g, int hop, cudaStream_t s);
+
+// ---- launchers (kh_sampled.cu) -----------------------------------------------
+// level i of the list recursion for `count` nodes (worklist == nullptr: all);
+// track != 0 records nodes whose (|B|, k) changed into the changed list.
+int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
+                 int64_t count_static, int track, cudaStream_t s);
+// neighbours (alive) of the nodes in `list` join the work list, deduplicated by stamp phase
+void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int phase,
+                            cudaStream_t s);
+
+// ---- launchers (kh_peel.cu) --------------------------------------------------
+int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, bool out_dev);
+int run_estimate_all(Graph& g);
+
+}  // namespace kh
+
+struct kh_ctx {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    int sm_count;
+    char err[512];
+};
+
+namespace kh {
+struct Graph {
+    kh_ctx* ctx;
+    int64_t n;
+    int64_t nnz;
+    int h;
+    uint64_t seed;
+    int64_t M;
+    int64_t cap;            // list slot capacity (>= M, multiple of 4)
+    bool ranks_valid;
+    bool lists_valid;       // lists hold the full-graph recursion for (h, M, seed)
+    int64_t *rowptr;
+    int32_t *col;
+    uint8_t *rank;
+    uint8_t *alive;
+    uint32_t *keys;
+    int64_t keys_levels;    // allocated levels in keys
+    int32_t *lsz;
+    uint8_t *lk;
+    int64_t lvl_alloc;      // allocated levels in lsz/lk
+    int32_t *d32;
+    unsigned long long *d64;
+    int32_t *core32;
+    unsigned long long *core64;
+    int32_t *round_of;
+    int32_t *seen;
+    int32_t *listR;
+    int32_t *listA;
+    int32_t *listB;
+    int32_t *listW;
+    int32_t *listC[2];
+    DevState *state;
+    // BFS scratch
+    int32_t *queues;
+    uint32_t *gbitmaps;
+    int64_t scratch_ctas;
+    // last peel statistics
+    int64_t last_rounds;
+    int64_t last_updates;
+    bool have_rounds;
+};
+}  // namespace kh
+
+struct kh_graph {
+    kh::Graph g;
+};
+
+namespace kh {
+// Utility: set the context error text; returns code.
+int set_error(kh_ctx* ctx, int code, const char* fmt, ...);
+// Ensure the per-graph work arrays exist (idempotent).
+int ensure_work(Graph& g);
+int ensure_lists(Graph& g);
+int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps);
+int check_cuda(kh_ctx* ctx, cudaError_t e, const char* what);
+}  // namespace kh
+
+#define KH_CUDA_TRY(ctx, expr)                                  \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return kh::check_cuda((ctx), _e, #expr); \
+    } while (0)

@@ -1,0 +1,437 @@
+// kh_sampled.cu -- the level recursion of the sampled lists B[v,i], k[v,i].
+//
+// Prop. 3.1: B[v,i] is the rank filter of T = {v} U B[w,i-1] (w alive
+// neighbours of v) at level k[v,i] >= max_w k[w,i-1], and Alg. 2 picks the
+// smallest level leaving at most M members.  Because N(w; i-1) is inside
+// N(v; i), the result equals {u in N(v;i,X) : r[u] >= kappa} with kappa the
+// smallest level whose rank-filtered N(v;i,X) has at most M members, so B and
+// k depend only on the alive set, the ranks and M.
+//
+// Level 1 (T = {v} plus alive neighbours, no repeats): one warp per node, a
+// 32-bin rank histogram, kappa from its suffix sums, a second pass writes the
+// members grouped by rank.
+//
+// Levels >= 2: one CTA per node with an open-addressing hash set of packed keys
+// (r << 27 | id) in shared memory.  Warps stream the neighbours' lists
+// (coalesced 32-key chunks).  A running threshold t starts at max_w k[w,i-1];
+// keys below t are skipped, and because each list is grouped by rank from the
+// highest, a warp stops reading a list at its first key below t.  After every
+// chunk step the CTA raises t to the smallest level whose count of distinct
+// keys is <= M (Alg. 5's trim), and compacts the set when dead entries pile
+// up.  The last level only needs |B[v,h]| and k[v,h] for the estimate of
+// Alg. 1, so it writes no list.
+//
+// A node's (|B|, k) pair changes exactly when B[v,i] or k[v,i] changes: with k
+// fixed, the new list is a subset of the old one (nodes only leave), so equal
+// sizes mean equal sets.  Changed nodes drive the next level's refresh (Alg. 3).
+#include "kh_internal.cuh"
+
+namespace kh {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr int kL1Threads = 256;
+constexpr int kLuThreads = 256;
+
+struct LevelArgs {
+    const int64_t* rowptr;
+    const int32_t* col;
+    const uint8_t* alive;
+    const uint8_t* rank;
+    int64_t n;
+    int level;
+    int last;                  // level == h
+    int64_t M;
+    int64_t cap;
+    const uint32_t* keys_in;   // lists of level-1 (levels >= 2)
+    uint32_t* keys_out;        // lists of this level (when !last)
+    const int32_t* lsz_in;
+    const uint8_t* lk_in;
+    int32_t* lsz_out;
+    uint8_t* lk_out;
+    unsigned long long* est;   // estimate (when last)
+    const int32_t* worklist;
+    const int* d_count;
+    int64_t count_static;
+    int track;
+    int32_t* changed;
+    int* n_changed;
+    int* work_ctr;
+    int* err;
+    unsigned long long* updates;
+};
+
+__device__ __forceinline__ unsigned long long estimate_of(int S, int kappa, int rv, int64_t M) {
+    // Alg. 1: d = |B[v,h] \ {v}| 2^k; if k > 0, d = max(d, M 2^(k-1))
+    const int T = S - (rv >= kappa ? 1 : 0);
+    unsigned long long d = (unsigned long long)T << kappa;
+    if (kappa > 0) {
+        const unsigned long long f = (unsigned long long)M << (kappa - 1);
+        if (f > d) d = f;
+    }
+    return d;
+}
+
+__device__ __forceinline__ void record_change(const LevelArgs& a, int v, int S, int kappa) {
+    const int old_s = a.lsz_out[v];
+    const int old_k = a.lk_out[v];
+    a.lsz_out[v] = S;
+    a.lk_out[v] = (uint8_t)kappa;
+    if (a.track && (old_s != S || old_k != kappa)) {
+        const int p = atomicAdd(a.n_changed, 1);
+        if (p < a.n) a.changed[p] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
+    __shared__ int s_hist[kL1Threads / 32][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int* hist = s_hist[wib];
+    const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < total; idx += nw) {
+        const int v = a.worklist ? a.worklist[idx] : (int)idx;
+        if (a.alive[v] != 1) continue;
+        hist[lane] = 0;
+        __syncwarp();
+        const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+        for (int64_t k0 = b; k0 < e; k0 += 32) {
+            const int64_t k = k0 + lane;
+            if (k < e) {
+                const int32_t u = a.col[k];
+                if (a.alive[u] == 1) atomicAdd(&hist[a.rank[u]], 1);
+            }
+        }
+        const int rv = a.rank[v];
+        if (lane == 0) atomicAdd(&hist[rv], 1);
+        __syncwarp();
+        // S_j = #{u in T : r[u] >= j}, lane j holds S_j
+        int S = hist[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const int t = __shfl_down_sync(kFull, S, off);
+            if (lane + off < 32) S += t;
+        }
+        const uint32_t over = __ballot_sync(kFull, S > a.M);
+        const int kappa = over ? 32 - __clz(over) : 0;
+        const int Sk = __shfl_sync(kFull, S, kappa & 31);
+        const int Skap = kappa < 32 ? Sk : 0;
+        if (a.last) {
+            if (lane == 0) {
+                a.est[v] = estimate_of(Skap, kappa, rv, a.M);
+                record_change(a, v, Skap, kappa);
+                atomicAdd(a.updates, 1ull);
+            }
+            continue;
+        }
+        // members grouped by rank, highest first: rank j starts at S_{j+1}
+        const int above = __shfl_down_sync(kFull, S, 1);
+        __syncwarp();
+        hist[lane] = lane < 31 ? above : 0;
+        __syncwarp();
+        uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
+        for (int64_t k0 = b; k0 < e; k0 += 32) {
+            const int64_t k = k0 + lane;
+            if (k < e) {
+                const int32_t u = a.col[k];
+                if (a.alive[u] == 1) {
+                    const int r = a.rank[u];
+                    if (r >= kappa) {
+                        const int p = atomicAdd(&hist[r], 1);
+                        if (p < a.cap) out[p] = ((uint32_t)r << kIdBits) | (uint32_t)u;
+                        else atomicOr(a.err, kErrList);
+                    }
+                }
+            }
+        }
+        if (lane == 0) {
+            if (rv >= kappa) {
+                const int p = atomicAdd(&hist[rv], 1);
+                if (p < a.cap) out[p] = ((uint32_t)rv << kIdBits) | (uint32_t)v;
+                else atomicOr(a.err, kErrList);
+            }
+            record_change(a, v, Skap, kappa);
+        }
+        __syncwarp();
+    }
+}
+
+// Insert `key` into the shared hash set; returns 1 if it was not there.
+__device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, int* err) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = ((key & kIdMask) * 0x9E3779B1u) >> (32 - lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t prev = atomicCAS(tab + s, kEmpty, key);
+        if (prev == kEmpty) return 1;
+        if (prev == key) return 0;
+        s = (s + 1u) & mask;
+    }
+    atomicOr(err, kErrProbe);
+    return 0;
+}
+
+__global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    const int hcap = 1 << lg;
+    uint32_t* tab = s_dyn;
+    uint32_t* stage = s_dyn + hcap;  // hcap / 2 entries
+    __shared__ int s_hist[32];
+    __shared__ int s_src, s_t, s_entries, s_nstage, s_compact;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+    for (;;) {
+        if (tid == 0) s_src = atomicAdd(a.work_ctr, 1);
+        __syncthreads();
+        const int64_t idx = s_src;
+        if (idx >= total) break;
+        const int v = a.worklist ? a.worklist[idx] : (int)idx;
+        if (a.alive[v] != 1) {
+            __syncthreads();
+            continue;
+        }
+        for (int i = tid; i < hcap; i += blockDim.x) tab[i] = kEmpty;
+        if (tid < 32) s_hist[tid] = 0;
+        if (tid == 0) {
+            s_t = 0;
+            s_entries = 0;
+        }
+        __syncthreads();
+        const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+        const int deg = (int)(e - b);
+        // t starts at max k[w,i-1] over alive neighbours (Prop. 3.1)
+        int myk = 0;
+        for (int64_t k = b + tid; k < e; k += blockDim.x) {
+            const int32_t w = a.col[k];
+            if (a.alive[w] == 1) myk = max(myk, (int)a.lk_in[w]);
+        }
+        for (int off = 16; off > 0; off >>= 1) myk = max(myk, __shfl_down_sync(kFull, myk, off));
+        if (lane == 0 && myk) atomicMax(&s_t, myk);
+        __syncthreads();
+        const int rv = a.rank[v];
+        if (tid == 0 && rv >= s_t) {
+            set_insert(tab, lg, ((uint32_t)rv << kIdBits) | (uint32_t)v, a.err);
+            s_hist[rv] += 1;
+            s_entries += 1;
+        }
+        __syncthreads();
+        // stream the neighbours' lists, one 32-key chunk per warp per step
+        int li = warp;  // neighbour index of this warp's current list
+        int pos = 0;
+        bool any = true;
+        while (any) {
+            const int t = *(volatile int*)&s_t;
+            // advance to an alive neighbour with a non-empty list (warp-uniform)
+            int32_t w = -1;
+            int sz = 0;
+            while (li < deg) {
+                w = a.col[b + li];
+                if (a.alive[w] == 1) {
+                    sz = min(a.lsz_in[w], (int)a.cap);
+                    if (sz > pos) break;
+                }
+                li += nwarps;
+                pos = 0;
+            }
+            if (li < deg) {
+                const uint32_t* L = a.keys_in + (size_t)w * (size_t)a.cap;
+                const int p = pos + lane;
+                const bool valid = p < sz;
+                const uint32_t key = valid ? L[p] : 0u;
+                const int r = (int)(key >> kIdBits);
+                if (valid && r >= t) {
+                    if (set_insert(tab, lg, key, a.err)) {
+                        atomicAdd(&s_hist[r], 1);
+                        atomicAdd(&s_entries, 1);
+                    }
+                }
+                const uint32_t below = __ballot_sync(kFull, valid && r < t);
+                if (below || pos + 32 >= sz) {
+                    li += nwarps;
+                    pos = 0;
+                } else {
+                    pos += 32;
+                }
+            }
+            any = __syncthreads_or(li < deg);
+            if (tid == 0) {
+                // smallest level >= t with at most M distinct members
+                int S = 0, tn = s_t;
+                for (int j = 31; j >= s_t; --j) {
+                    S += s_hist[j];
+                    if (S > a.M) {
+                        tn = j + 1;
+                        break;
+                    }
+                }
+                s_t = tn;
+                s_compact = s_entries > (hcap >> 1);
+                s_nstage = 0;
+            }
+            __syncthreads();
+            if (s_compact) {
+                const int tc = s_t;
+                for (int i = tid; i < hcap; i += blockDim.x) {
+                    const uint32_t key = tab[i];
+                    if (key != kEmpty && (int)(key >> kIdBits) >= tc) {
+                        const int p = atomicAdd(&s_nstage, 1);
+                        if (p < (hcap >> 1)) stage[p] = key;
+                        else atomicOr(a.err, kErrProbe);
+                    }
+                }
+                __syncthreads();
+                for (int i = tid; i < hcap; i += blockDim.x) tab[i] = kEmpty;
+                __syncthreads();
+                const int ns = min(s_nstage, hcap >> 1);
+                for (int i = tid; i < ns; i += blockDim.x) set_insert(tab, lg, stage[i], a.err);
+                if (tid == 0) s_entries = ns;
+                __syncthreads();
+            }
+        }
+        const int kappa = s_t;
+        int S = 0;
+        for (int j = kappa; j < 32; ++j) S += s_hist[j];
+        __syncthreads();
+        if (a.last) {
+            if (tid == 0) {
+                a.est[v] = estimate_of(S, kappa, rv, a.M);
+                record_change(a, v, S, kappa);
+                atomicAdd(a.updates, 1ull);
+            }
+        } else {
+            // write members grouped by rank, highest first
+            if (tid < 32) {
+                int above = 0;
+                for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
+                s_hist[tid] = above;  // start offset of rank tid
+            }
+            __syncthreads();
+            uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
+            for (int i = tid; i < hcap; i += blockDim.x) {
+                const uint32_t key = tab[i];
+                if (key != kEmpty) {
+                    const int r = (int)(key >> kIdBits);
+                    if (r >= kappa) {
+                        const int p = atomicAdd(&s_hist[r], 1);
+                        if (p < a.cap) out[p] = key;
+                        else atomicOr(a.err, kErrList);
+                    }
+                }
+            }
+            if (tid == 0) record_change(a, v, S, kappa);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
+                            const int32_t* __restrict__ list, const int* __restrict__ nlist,
+                            int32_t* __restrict__ wl, int* nwl, const DevState* __restrict__ st,
+                            int phase, int64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const int nin = *nlist;
+    const int stamp = st->round * kPhaseStride + phase;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
+        const int w = list[i];
+        const int64_t b = rowptr[w], e = rowptr[w + 1];
+        for (int64_t k0 = b; k0 < e; k0 += 32) {
+            const int64_t k = k0 + lane;
+            bool isnew = false;
+            int32_t u = 0;
+            if (k < e) {
+                u = col[k];
+                if (alive[u] == 1 && *(volatile int32_t*)(seen + u) != stamp)
+                    isnew = atomicExch(seen + u, stamp) != stamp;
+            }
+            const uint32_t m = __ballot_sync(kFull, isnew);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(nwl, __popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (isnew) {
+                const int p = base + __popc(m & ((1u << lane) - 1u));
+                if (p < cap) wl[p] = u;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int table_lg(int64_t M) {
+    // capacity >= 2 (M + threads) rounded up to a power of two
+    int lg = 10;
+    while ((int64_t(1) << lg) < 2 * (M + kLuThreads)) ++lg;
+    return lg;
+}
+
+int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
+                 int64_t count_static, int track, cudaStream_t s) {
+    if (g.n == 0) return KH_OK;
+    if (!worklist && count_static == 0) return KH_OK;
+    LevelArgs a;
+    a.rowptr = g.rowptr;
+    a.col = g.col;
+    a.alive = g.alive;
+    a.rank = g.rank;
+    a.n = g.n;
+    a.level = level;
+    a.last = level == g.h;
+    a.M = g.M;
+    a.cap = g.cap;
+    a.keys_in = level >= 2 ? g.keys + (size_t)(level - 2) * (size_t)g.n * (size_t)g.cap : nullptr;
+    a.keys_out = level < g.h ? g.keys + (size_t)(level - 1) * (size_t)g.n * (size_t)g.cap : nullptr;
+    a.lsz_in = level >= 2 ? g.lsz + (size_t)(level - 2) * g.n : nullptr;
+    a.lk_in = level >= 2 ? g.lk + (size_t)(level - 2) * g.n : nullptr;
+    a.lsz_out = g.lsz + (size_t)(level - 1) * g.n;
+    a.lk_out = g.lk + (size_t)(level - 1) * g.n;
+    a.est = g.d64;
+    a.worklist = worklist;
+    a.d_count = d_count;
+    a.count_static = count_static;
+    a.track = track;
+    a.changed = g.listC[level & 1];
+    a.n_changed = &g.state->nC[level & 1];
+    a.work_ctr = &g.state->work_ctr[1];
+    a.err = &g.state->err;
+    a.updates = &g.state->updates;
+    cudaError_t e;
+    if (track) {
+        e = cudaMemsetAsync(a.n_changed, 0, sizeof(int), s);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_changed");
+    }
+    const int64_t work = worklist ? g.n : count_static;
+    if (level == 1) {
+        int64_t grid = (work + (kL1Threads / 32) - 1) / (kL1Threads / 32);
+        const int64_t gmax = (int64_t)g.ctx->sm_count * 8;
+        if (grid > gmax) grid = gmax;
+        if (grid < 1) grid = 1;
+        k_level1<<<(int)grid, kL1Threads, 0, s>>>(a);
+        return KH_OK;
+    }
+    const int lg = table_lg(g.M);
+    const size_t dyn = (size_t)(1 << lg) * 4 + (size_t)(1 << (lg - 1)) * 4;
+    e = cudaFuncSetAttribute(k_levelU, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levelU, kLuThreads, dyn);
+    if (e != cudaSuccess) return check_cuda(g.ctx, e, "occupancy(k_levelU)");
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)g.ctx->sm_count * per_sm;
+    if (work < grid) grid = work;
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
+    if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    k_levelU<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
+    return KH_OK;
+}
+
+void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int phase,
+                            cudaStream_t s) {
+    const int grid = g.ctx->sm_count * 8;
+    k_mark_nbrs<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, list, d_count, g.listW,
+                                     &g.state->nW, g.state, phase, g.n);
+}
+
+}  // namespace kh

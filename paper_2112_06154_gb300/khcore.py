@@ -1,0 +1,269 @@
+"""Thin Python binding of the C ABI in ``include/khcore.h``.
+
+Functions carry the C names and only marshal arguments: every step of the
+path runs in the CUDA library ``_build/libkhcore.so``.  Host arrays are numpy;
+device arrays are torch CUDA tensors (their ``data_ptr()`` is passed with
+``KH_DEVICE_PTR``).  Loading fails loudly when the library is missing; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KH_OK = 0
+KH_EINVAL = -1
+KH_EGRAPH = -2
+KH_ENOMEM = -3
+KH_ECUDA = -4
+KH_ETIMEOUT = -5
+KH_EINTERNAL = -6
+KH_DEVICE_PTR = 1
+
+_ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",
+             KH_ECUDA: "KH_ECUDA", KH_ETIMEOUT: "KH_ETIMEOUT", KH_EINTERNAL: "KH_EINTERNAL"}
+
+# (name, restype, argtypes) of every entry point declared in include/khcore.h
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("kh_ctx_create", ctypes.c_int, [_PP, ctypes.c_int, _P]),
+    ("kh_ctx_destroy", ctypes.c_int, [_P]),
+    ("kh_last_error", ctypes.c_char_p, [_P]),
+    ("kh_graph_load_csr", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _PP]),
+    ("kh_graph_free", ctypes.c_int, [_P]),
+    ("kh_graph_n", ctypes.c_int, [_P, _I64P]),
+    ("kh_set_h", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("kh_set_sampling", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_double]),
+    ("kh_get_M", ctypes.c_int, [_P, _I64P]),
+    ("kh_ranks", ctypes.c_int, [_P, _P, ctypes.c_uint32]),
+    ("kh_hdegree_exact", ctypes.c_int, [_P, _P, ctypes.c_uint32]),
+    ("kh_sampled_counts", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_uint32]),
+    ("kh_estimate", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_uint32]),
+    ("kh_core_exact", ctypes.c_int, [_P, _P, ctypes.c_uint32]),
+    ("kh_core_sampled", ctypes.c_int, [_P, _P, ctypes.c_uint32]),
+    ("kh_peel_info", ctypes.c_int, [_P, _P, _I64P, _I64P]),
+    ("kh_sync", ctypes.c_int, [_P]),
+]
+
+_lib = None
+
+
+class KhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libkhcore.so (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Ctx:
+    """Owner of a ``kh_ctx*``."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def error(self) -> str:
+        return load().kh_last_error(self.handle).decode(errors="replace")
+
+    def close(self):
+        if self.handle:
+            load().kh_ctx_destroy(self.handle)
+            self.handle = None
+
+
+class Graph:
+    """Owner of a ``kh_graph*`` (keeps its context alive)."""
+
+    def __init__(self, ctx: Ctx, handle, n: int):
+        self.ctx = ctx
+        self.handle = handle
+        self.n = n
+
+    def close(self):
+        if self.handle:
+            load().kh_graph_free(self.handle)
+            self.handle = None
+
+
+def _check(rc, ctx: Ctx):
+    if rc != KH_OK:
+        raise KhError(rc, ctx.error() if ctx is not None else "")
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, is_device) for a numpy array or a torch tensor."""
+    if x is None:
+        return None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x.is_cuda
+    if not x.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data), False
+
+
+def kh_ctx_create(device: int = 0, stream=None) -> Ctx:
+    """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    h = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = load().kh_ctx_create(ctypes.byref(h), device, s)
+    if rc != KH_OK:
+        raise KhError(rc, "kh_ctx_create failed")
+    return Ctx(h)
+
+
+def kh_ctx_destroy(ctx: Ctx):
+    ctx.close()
+
+
+def kh_last_error(ctx: Ctx) -> str:
+    return ctx.error()
+
+
+def kh_graph_load_csr(ctx: Ctx, rowptr, col) -> Graph:
+    """rowptr int64[n+1], col int32[nnz]: both numpy (host) or both torch CUDA tensors."""
+    if _is_torch(rowptr):
+        import torch
+        assert rowptr.dtype == torch.int64 and col.dtype == torch.int32
+    else:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+    n = int(rowptr.shape[0]) - 1
+    pr, dev = _ptr(rowptr)
+    pc, _ = _ptr(col)
+    h = ctypes.c_void_p()
+    rc = load().kh_graph_load_csr(ctx.handle, n, pr, pc, KH_DEVICE_PTR if dev else 0,
+                                  ctypes.byref(h))
+    _check(rc, ctx)
+    return Graph(ctx, h, n)
+
+
+def kh_graph_free(g: Graph):
+    g.close()
+
+
+def kh_set_h(g: Graph, h: int):
+    _check(load().kh_set_h(g.handle, h), g.ctx)
+
+
+def kh_set_sampling(g: Graph, seed: int = 1, M: int = 0, eps: float = 0.5, delta: float = 0.05):
+    _check(load().kh_set_sampling(g.handle, seed, M, eps, delta), g.ctx)
+
+
+def kh_get_M(g: Graph) -> int:
+    m = ctypes.c_int64()
+    _check(load().kh_get_M(g.handle, ctypes.byref(m)), g.ctx)
+    return int(m.value)
+
+
+def _out(out, n, dtype, cols=None):
+    if out is not None:
+        return out
+    shape = (n,) if cols is None else (n, max(cols, 0))
+    return np.zeros(shape, dtype=dtype)
+
+
+def kh_ranks(g: Graph, out=None):
+    out = _out(out, g.n, np.uint8)
+    p, dev = _ptr(out)
+    _check(load().kh_ranks(g.handle, p, KH_DEVICE_PTR if dev else 0), g.ctx)
+    return out
+
+
+def kh_hdegree_exact(g: Graph, out=None):
+    out = _out(out, g.n, np.int32)
+    p, dev = _ptr(out)
+    _check(load().kh_hdegree_exact(g.handle, p, KH_DEVICE_PTR if dev else 0), g.ctx)
+    return out
+
+
+def kh_sampled_counts(g: Graph, j_lo: int, j_hi: int, out=None):
+    out = _out(out, g.n, np.int32, j_hi - j_lo + 1)
+    p, dev = _ptr(out)
+    _check(load().kh_sampled_counts(g.handle, j_lo, j_hi, p, KH_DEVICE_PTR if dev else 0), g.ctx)
+    return out
+
+
+def kh_estimate(g: Graph, est=None, level=None, bsize=None):
+    """Returns (est uint64, level uint8, bsize int32)."""
+    est = _out(est, g.n, np.uint64)
+    dev = _ptr(est)[1]
+    if level is None and not dev:
+        level = np.zeros(g.n, np.uint8)
+    if bsize is None and not dev:
+        bsize = np.zeros(g.n, np.int32)
+    pe, _ = _ptr(est)
+    pl, _ = _ptr(level)
+    pb, _ = _ptr(bsize)
+    _check(load().kh_estimate(g.handle, pe, pl, pb, KH_DEVICE_PTR if dev else 0), g.ctx)
+    return est, level, bsize
+
+
+def kh_core_exact(g: Graph, out=None):
+    out = _out(out, g.n, np.int32)
+    p, dev = _ptr(out)
+    _check(load().kh_core_exact(g.handle, p, KH_DEVICE_PTR if dev else 0), g.ctx)
+    return out
+
+
+def kh_core_sampled(g: Graph, out=None):
+    out = _out(out, g.n, np.uint64)
+    p, dev = _ptr(out)
+    _check(load().kh_core_sampled(g.handle, p, KH_DEVICE_PTR if dev else 0), g.ctx)
+    return out
+
+
+def kh_peel_info(g: Graph, want_rounds: bool = True):
+    """(round_of int32[n] or None, rounds, updates) of the last kh_core_* call."""
+    ro = np.zeros(g.n, np.int32) if want_rounds else None
+    rounds = ctypes.c_int64()
+    updates = ctypes.c_int64()
+    p, _ = _ptr(ro)
+    _check(load().kh_peel_info(g.handle, p, ctypes.byref(rounds), ctypes.byref(updates)), g.ctx)
+    return ro, int(rounds.value), int(updates.value)
+
+
+def kh_sync(g: Graph):
+    _check(load().kh_sync(g.handle), g.ctx)
+
+
+def kh_graph_n(g: Graph) -> int:
+    n = ctypes.c_int64()
+    _check(load().kh_graph_n(g.handle, ctypes.byref(n)), g.ctx)
+    return int(n.value)
