@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the (k,h)-core hot path on one GB300 (or N replicas).
+
+Workload: seeded Chung-Lu power-law graph, n = 200,000, about 2M undirected
+edges, degree exponent 2.5, maximum expected degree 5,000 (graph seed 1002),
+at h = 2 and h = 3, eps = 0.5, delta = 0.05 (M = 719), rank seed 1.
+
+One step is one pass of the whole hot path over that graph:
+  for h in (2, 3): ranks; exact h-degrees; fixed-level counts j = 0..10
+                   (sampling probability 1 .. 1/1024); adaptive estimate;
+                   sampled (k,h)-core decomposition (Core, Alg. 4);
+  then the exact (k,2)-core decomposition (ExactCore, with early stop).
+The metric is h-degree updates per second: one update is one (re)computation
+of one alive node's h-degree or of its B[.,h] and estimate (initial passes
+count n each).  ms_per_step is the wall time of that whole decomposition pass.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload: exact h-degrees of all nodes at h = 2 per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "(k,h)-core decomposition: h-degree updates/s"
+UNIT = "updates/s"
+N_NODES, AVG_DEG, GAMMA, MAX_DEG, GRAPH_SEED = 200_000, 20, 2.5, 5000, 1002
+HS = (2, 3)
+EPS, DELTA, RANK_SEED = 0.5, 0.05, 1
+J_LO, J_HI = 0, 10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_graph():
+    from paper_2112_06154_gb300 import graphgen as gg
+    return gg.chung_lu(N_NODES, AVG_DEG, GAMMA, MAX_DEG, GRAPH_SEED)
+
+
+def config(rp, cl, M):
+    return {
+        "workload": "chung_lu_n200k_m2M_gamma2.5_h2_h3",
+        "graph": "Chung-Lu power law (synthetic stand-in for the paper's social graphs)",
+        "n": int(rp.size - 1), "m": int(cl.size // 2), "max_deg": int(np.diff(rp).max()),
+        "h": list(HS), "eps": EPS, "delta": DELTA, "M": int(M), "rank_seed": RANK_SEED,
+        "graph_seed": GRAPH_SEED, "fixed_levels": [J_LO, J_HI],
+        "step": "per h: ranks, exact h-degrees, fixed-level counts, adaptive estimate, "
+                "sampled core; plus exact (k,2)-core",
+        "l2": "flushed (512 MB write) between timed steps",
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def load_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kind_name):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 2 and parts[0] == kind_name and not line.startswith("#"):
+                    return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    from paper_2112_06154_gb300 import khcore as K
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    K.load(build_if_missing=True)
+    rp, cl = make_graph()
+    n = rp.size - 1
+    stream = torch.cuda.Stream()
+    ctx = K.kh_ctx_create(dev, stream)
+    G = K.kh_graph_load_csr(ctx, rp, cl)
+    K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+    M = K.kh_get_M(G)
+    nj = J_HI - J_LO + 1
+    td = lambda *shape, dt: torch.empty(*shape, dtype=dt, device="cuda")
+    out = {
+        "r": td(n, dt=torch.uint8), "deg": td(n, dt=torch.int32), "cnt": td(n, nj, dt=torch.int32),
+        "est": td(n, dt=torch.int64), "lvl": td(n, dt=torch.uint8), "bs": td(n, dt=torch.int32),
+        "cs": td(n, dt=torch.int64), "ce": td(n, dt=torch.int32),
+    }
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(graph, host):
+        updates = 0
+        for h in HS:
+            K.kh_set_h(graph, h)
+            if host:
+                K.kh_ranks(graph)
+                K.kh_hdegree_exact(graph)
+                K.kh_sampled_counts(graph, J_LO, J_HI)
+                K.kh_estimate(graph)
+                K.kh_core_sampled(graph)
+            else:
+                K.kh_ranks(graph, out["r"])
+                K.kh_hdegree_exact(graph, out["deg"])
+                K.kh_sampled_counts(graph, J_LO, J_HI, out["cnt"])
+                K.kh_estimate(graph, out["est"], out["lvl"], out["bs"])
+                K.kh_core_sampled(graph, out["cs"])
+            updates += 3 * n + K.kh_peel_info(graph, False)[2]
+        K.kh_set_h(graph, 2)
+        if host:
+            K.kh_core_exact(graph)
+        else:
+            K.kh_core_exact(graph, out["ce"])
+        updates += K.kh_peel_info(graph, False)[2]
+        return updates
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(G, False)
+        K.kh_sync(G)
+    clocks = Clocks(dev if world == 1 else local)
+    total_ms = 0.0
+    total_updates = 0
+    launches0 = K.kh_launch_count(G)
+    clocks.start()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        total_updates += step(G, False)
+        e1.record(stream)
+        barrier()
+        total_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = K.kh_launch_count(G) - launches0
+
+    # e2e: the same steps through the C ABI with host buffers, graph upload included
+    e2e = None
+    if not args.no_e2e:
+        h2d = rp.nbytes + cl.nbytes
+        d2h = 0
+        for h in HS:
+            d2h += n * (1 + 4 + 4 * nj + 8 + 1 + 4 + 8)
+        d2h += 4 * n
+        Gw = K.kh_graph_load_csr(ctx, rp, cl)   # warm-up
+        K.kh_set_sampling(Gw, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+        step(Gw, True)
+        Gw.close()
+        barrier()
+        t_e2e = 0.0
+        upd_e2e = 0
+        for _ in range(args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            Ge = K.kh_graph_load_csr(ctx, rp, cl)
+            K.kh_set_sampling(Ge, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+            upd_e2e += step(Ge, True)
+            K.kh_sync(Ge)
+            t_e2e += time.perf_counter() - t0
+            Ge.close()
+        e2e = {"value": upd_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # roofline: one extra profiled step (kernel classes timed with CUDA events
+    # on the library's stream, algorithmic bytes counted on the device)
+    K.kh_prof_enable(G, True)
+    step(G, False)
+    prof = {}
+    for kind in range(K.KH_PROF_KINDS):
+        ms, nl, byts = K.kh_prof_read(G, kind)
+        prof[K.PROF_NAMES[kind]] = {"ms": ms, "launches": nl, "alg_bytes": byts}
+    K.kh_prof_enable(G, False)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    peak, peak_src = load_peak()
+    achieved = (d["alg_bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
+    traffic = profile_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic,
+                "alg_bytes_per_launch": d["alg_bytes"] / max(d["launches"], 1),
+                "avg_launch_ms": d["ms"] / max(d["launches"], 1),
+                "peak_source": f"{peak_src} hbm_gbs (copy)",
+                "timing": "kernel-class CUDA events on the library stream, one profiled step "
+                          "after the timed region",
+                "classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                                "GBps": round(v["alg_bytes"] / 1e6 / v["ms"], 1) if v["ms"] else 0}
+                            for k, v in prof.items()}}
+
+    # max over ranks
+    per_rank = torch.tensor([total_ms, float(total_updates)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        t = per_rank.clone()
+        dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        total_ms_max, updates_all = float(t[0]), float(t[1])
+    else:
+        total_ms_max, updates_all = total_ms, float(total_updates)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(rp, cl, M)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": updates_all / (total_ms_max / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded Chung-Lu graph; no dataset)",
+            "config": config(rp, cl, M), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "updates_per_step": total_updates / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(rp, cl, M):
+    """The oracle, single-threaded: exact h-degrees (h=2) and the adaptive
+    estimate through the level recursion (h=2) of every node of the graph."""
+    import oracle as O
+    n = rp.size - 1
+    r = O.ranks(n, RANK_SEED)
+    t0 = time.perf_counter()
+    O.hdegree_exact(rp, cl, 2)
+    O.estimate_dp(rp, cl, r, 2, M)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"exact h-degrees + level-recursion estimate, h=2, all {n} nodes "
+                      f"of the same graph ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    rp, cl = make_graph()
+    n = rp.size - 1
+    M = O.budget_M(n, EPS, DELTA)
+    for _ in range(args.warmup):
+        O.hdegree_some(rp, cl, 2, np.arange(0, n, 50))
+    t = 0.0
+    upd = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.hdegree_exact(rp, cl, 2)
+        t += time.perf_counter() - t0
+        upd += n
+    value = upd / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded Chung-Lu graph; no dataset)", "config": config(rp, cl, M),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"exact h-degrees, h=2, all {n} nodes per step "
+                                   "(single-threaded CPU oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

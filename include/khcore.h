@@ -81,7 +81,7 @@ int kh_set_h(kh_graph *g, int32_t h);
  * (r[v] = trailing zeros of the v-th output, capped at 31).  M_or_0 > 0 sets
  * M directly; M_or_0 == 0 sets M = floor(1 + 4(2+eps)/eps^2 (log(2n/delta) +
  * log 8)) (Eq. (buffer), natural log).  Requires eps > 0, 0 < delta < 1 when
- * M_or_0 == 0; M must lie in [1, 16000].  Default: seed 1, eps 0.5,
+ * M_or_0 == 0; M must lie in [1, 12000].  Default: seed 1, eps 0.5,
  * delta 0.05. */
 int kh_set_sampling(kh_graph *g, uint64_t seed, int64_t M_or_0, double eps, double delta);
 
@@ -123,6 +123,29 @@ int kh_core_sampled(kh_graph *g, uint64_t *core, uint32_t flags);
  * *updates the number of node (re)computations including the initial pass.
  * Host pointers only. */
 int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updates);
+
+/* Profiling of kernel classes (no counterpart in the paper; measurement aid).
+ * kh_prof_enable(g, 1) resets the counters and brackets every later launch of
+ * each kernel class with CUDA events on the context stream (peeling rounds
+ * are then launched one by one instead of through a CUDA graph);
+ * kh_prof_enable(g, 0) stops the brackets and keeps the counters.
+ * kh_prof_read returns, for one class, the summed event time in ms, the number
+ * of bracketed launches and the algorithmic bytes the class moved (counted on
+ * the device: 8 + 4 deg per expanded vertex for the BFS, 4 per list key read
+ * and written for the list kernels, plus per-node metadata). */
+#define KH_PROF_BFS 0      /* exact h-degree / fixed-level count BFS */
+#define KH_PROF_LEVEL1 1   /* level-1 lists (Alg. 2 at i = 1) */
+#define KH_PROF_LEVELU 2   /* level >= 2 lists (Alg. 2 with Alg. 5's trim) */
+#define KH_PROF_FRONTIER 3 /* removed-set balls and refresh work lists */
+#define KH_PROF_PEEL 4     /* min / select / finish of each round */
+#define KH_PROF_KINDS 5
+int kh_prof_enable(kh_graph *g, int32_t on);
+int kh_prof_read(kh_graph *g, int32_t kind, double *ms, int64_t *launches, double *alg_bytes);
+
+/* Number of CUDA kernels the library has launched for this graph since it was
+ * loaded (kernels inside a replayed CUDA graph count one each per replay).
+ * No counterpart in the paper; measurement aid. */
+int kh_launch_count(kh_graph *g, int64_t *launches);
 
 /* Wait for all work enqueued on the graph's context stream. */
 int kh_sync(kh_graph *g);

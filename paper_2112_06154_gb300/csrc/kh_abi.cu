@@ -62,6 +62,61 @@ int ensure_work(Graph& g) {
     if ((rc = dalloc(g.ctx, &g.listW, n, "listW"))) return rc;
     if ((rc = dalloc(g.ctx, &g.listC[0], n, "listC0"))) return rc;
     if ((rc = dalloc(g.ctx, &g.listC[1], n, "listC1"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.listH, n, "listH"))) return rc;
+    return KH_OK;
+}
+
+static cudaEvent_t pool_event(Graph& g) {
+    if (!g.ev_pool) g.ev_pool = new std::vector<cudaEvent_t>();
+    if (!g.ev_pool->empty()) {
+        cudaEvent_t e = g.ev_pool->back();
+        g.ev_pool->pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void prof_begin(Graph& g, int kind, cudaStream_t s) {
+    if (!g.prof_on) return;
+    cudaEvent_t e = pool_event(g);
+    if (!e) return;
+    cudaEventRecord(e, s);
+    g.prof_kind->push_back(kind);
+    g.prof_ev->push_back(e);
+}
+
+void prof_end(Graph& g, int kind, cudaStream_t s) {
+    if (!g.prof_on) return;
+    (void)kind;
+    cudaEvent_t e = pool_event(g);
+    if (!e) return;
+    cudaEventRecord(e, s);
+    g.prof_ev->push_back(e);
+}
+
+// Fold recorded event pairs into the per-kind totals (synchronizes the stream).
+static int prof_collect(Graph& g) {
+    if (!g.prof_ev || g.prof_ev->empty()) return KH_OK;
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(g.ctx->stream));
+    const size_t pairs = g.prof_kind->size();
+    for (size_t i = 0; i < pairs && 2 * i + 1 < g.prof_ev->size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, (*g.prof_ev)[2 * i], (*g.prof_ev)[2 * i + 1]) == cudaSuccess) {
+            const int k = (*g.prof_kind)[i];
+            g.prof_ms[k] += ms;
+            g.prof_launches[k] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    for (cudaEvent_t e : *g.prof_ev) g.ev_pool->push_back(e);
+    g.prof_ev->clear();
+    g.prof_kind->clear();
     return KH_OK;
 }
 
@@ -136,6 +191,21 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.state);
     dfree(&g.queues);
     dfree(&g.gbitmaps);
+    dfree(&g.listH);
+    if (g.round_exec) cudaGraphExecDestroy(g.round_exec);
+    g.round_exec = nullptr;
+    if (g.ev_pool) {
+        for (cudaEvent_t e : *g.ev_pool) cudaEventDestroy(e);
+        delete g.ev_pool;
+        g.ev_pool = nullptr;
+    }
+    if (g.prof_ev) {
+        for (cudaEvent_t e : *g.prof_ev) cudaEventDestroy(e);
+        delete g.prof_ev;
+        g.prof_ev = nullptr;
+    }
+    delete g.prof_kind;
+    g.prof_kind = nullptr;
 }
 
 static int set_M(Graph& g, int64_t M) {
@@ -442,6 +512,47 @@ int kh_peel_info(kh_graph* G, int32_t* round_of, int64_t* rounds, int64_t* updat
         cudaSetDevice(g.ctx->device);
         return kh::copy_out(g, round_of, g.round_of, sizeof(int32_t) * (size_t)g.n, 0);
     }
+    return KH_OK;
+}
+
+int kh_prof_enable(kh_graph* G, int32_t on) {
+    if (!G) return KH_EINVAL;
+    Graph& g = G->g;
+    cudaSetDevice(g.ctx->device);
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(g.ctx->stream));
+    if (!g.prof_ev) g.prof_ev = new std::vector<cudaEvent_t>();
+    if (!g.prof_kind) g.prof_kind = new std::vector<int>();
+    if (!g.ev_pool) g.ev_pool = new std::vector<cudaEvent_t>();
+    for (cudaEvent_t e : *g.prof_ev) g.ev_pool->push_back(e);
+    g.prof_ev->clear();
+    g.prof_kind->clear();
+    for (int k = 0; k < kh::kProfKinds; ++k) {
+        g.prof_ms[k] = 0.0;
+        g.prof_launches[k] = 0;
+    }
+    KH_CUDA_TRY(g.ctx, cudaMemset(g.state->bytes, 0, sizeof(g.state->bytes)));
+    g.prof_on = on != 0;
+    return KH_OK;
+}
+
+int kh_prof_read(kh_graph* G, int32_t kind, double* ms, int64_t* launches, double* alg_bytes) {
+    if (!G) return KH_EINVAL;
+    Graph& g = G->g;
+    if (kind < 0 || kind >= kh::kProfKinds) return kh::set_error(g.ctx, KH_EINVAL, "bad profiling kind");
+    cudaSetDevice(g.ctx->device);
+    int rc = kh::prof_collect(g);
+    if (rc) return rc;
+    unsigned long long b = 0;
+    KH_CUDA_TRY(g.ctx, cudaMemcpy(&b, &g.state->bytes[kind], sizeof(b), cudaMemcpyDeviceToHost));
+    if (ms) *ms = g.prof_ms[kind];
+    if (launches) *launches = g.prof_launches[kind];
+    if (alg_bytes) *alg_bytes = (double)b;
+    return KH_OK;
+}
+
+int kh_launch_count(kh_graph* G, int64_t* launches) {
+    if (!G || !launches) return KH_EINVAL;
+    *launches = G->g.launches;
     return KH_OK;
 }
 

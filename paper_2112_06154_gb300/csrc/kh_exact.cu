@@ -97,6 +97,8 @@ struct BfsArgs {
     int* work_ctr;
     int* err;
     unsigned long long* updates;
+    unsigned long long* bytes;  // algorithmic bytes: 8 + 4 deg per expanded vertex, 4 per result
+    const int* skip;            // nonzero: the exact early stop fired, nothing to do
 };
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
@@ -143,7 +145,9 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     uint32_t* bm = SMEM ? s_bm_dyn : a.gbitmaps + (size_t)blockIdx.x * (size_t)a.words;
     int32_t* q = a.queues + (size_t)blockIdx.x * (size_t)a.qcap;
-    const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+    const int64_t total = (a.skip && *a.skip) ? 0 : (a.worklist ? (int64_t)(*a.d_count) : a.count_static);
+    if (total == 0) return;
+    unsigned long long my_bytes = 0;
 
     for (int i = tid; i < a.words; i += blockDim.x) bm[i] = 0u;
     __syncthreads();
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             for (int i = fs + warp; i < fe; i += nwarps) {
                 const int w = q[i];
                 const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
+                if (lane == 0) my_bytes += 8ull + 4ull * (unsigned long long)(e - b);
                 if (single || e - b >= kHeavyDeg) {
                     int slot = 0;
                     if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
@@ -219,6 +224,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
         if (tid == 0) {
             a.deg[v] = s_count;
             atomicAdd(a.updates, 1ull);
+            my_bytes += 4ull + (RANKS ? 4ull * (unsigned long long)a.nj : 0ull);
         }
         if (RANKS && tid < a.nj) {
             int c = 0;
@@ -237,6 +243,8 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
         }
         __syncthreads();
     }
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
 // One hop of the ball around the removed set R in the OLD graph (alive != 0):
@@ -246,14 +254,18 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
                            const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                            const int32_t* __restrict__ fin, const int* __restrict__ nfin,
                            int32_t* __restrict__ fout, int* nfout, int32_t* __restrict__ wl, int* nwl,
-                           const DevState* __restrict__ st, int push_next, int64_t cap) {
+                           const DevState* __restrict__ st, int push_next, int64_t cap,
+                           unsigned long long* bytes) {
+    if (st->early) return;
     const int lane = threadIdx.x & 31;
     const int nin = *nfin;
+    unsigned long long my_bytes = 0;
     const int stamp = st->round * kPhaseStride;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
         const int w = fin[i];
         const int64_t b = rowptr[w], e = rowptr[w + 1];
+        if (lane == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
         for (int64_t k0 = b; k0 < e; k0 += 32) {
             const int64_t k = k0 + lane;
             bool isnew = false;
@@ -285,6 +297,7 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
             }
         }
     }
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 int pick_grid(int sm, int per_sm, int64_t work) {
@@ -299,12 +312,14 @@ void launch_ranks(const Graph& g, cudaStream_t s) {
     if (g.n == 0) return;
     const int grid = pick_grid(g.ctx->sm_count, 4, (g.n + 255) / 256);
     k_ranks<<<grid, 256, 0, s>>>(g.rank, g.n, g.seed);
+    count_launch(const_cast<Graph&>(g), 1);
 }
 
 void launch_validate(const Graph& g, int* d_err, cudaStream_t s) {
     if (g.n == 0) return;
     const int grid = pick_grid(g.ctx->sm_count, 8, (g.n * 32 + 255) / 256);
     k_validate<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.n, g.nnz, d_err);
+    count_launch(const_cast<Graph&>(g), 1);
 }
 
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
@@ -352,9 +367,14 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.work_ctr = &g.state->work_ctr[0];
     a.err = &g.state->err;
     a.updates = &g.state->updates;
+    a.bytes = &g.state->bytes[kProfBfs];
+    a.skip = worklist ? &g.state->early : nullptr;
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    prof_begin(g, kProfBfs, s);
     kern<<<grid, kBfsThreads, dyn, s>>>(a);
+    count_launch(g, 1);
+    prof_end(g, kProfBfs, s);
     return KH_OK;
 }
 
@@ -366,8 +386,12 @@ void launch_ball_hop(Graph& g, int hop, cudaStream_t s) {
     int* nfout = &g.state->nF[hop & 1];
     cudaMemsetAsync(nfout, 0, sizeof(int), s);
     const int grid = g.ctx->sm_count * 8;
+    prof_begin(g, kProfFrontier, s);
     k_ball_hop<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, fin, nfin, fout, nfout,
-                                    g.listW, &g.state->nW, g.state, hop < g.h ? 1 : 0, g.n);
+                                    g.listW, &g.state->nW, g.state, hop < g.h ? 1 : 0, g.n,
+                                    &g.state->bytes[kProfFrontier]);
+    count_launch(g, 1);
+    prof_end(g, kProfFrontier, s);
 }
 
 }  // namespace kh

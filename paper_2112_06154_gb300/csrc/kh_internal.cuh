@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/khcore.h"
 
 namespace kh {
@@ -28,7 +30,7 @@ namespace kh {
 constexpr int kRankBits = 5;
 constexpr int kIdBits = 27;
 constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
-constexpr int kMaxM = 16000;
+constexpr int kMaxM = 12000;
 constexpr int kMaxH = 16;
 constexpr int kPhaseStride = 32;  // stamp = round * kPhaseStride + phase
 // Shared-memory visited bitmap limit per CTA (bytes); larger n uses global scratch.
@@ -39,6 +41,14 @@ constexpr int kErrQueue = 1;   // BFS queue overflow
 constexpr int kErrProbe = 2;   // hash probe limit reached
 constexpr int kErrList = 4;    // list larger than its slot
 constexpr int kErrGraph = 8;   // CSR validation failure
+
+// Kernel classes for the profiling counters (kh_prof_read kinds).
+constexpr int kProfBfs = 0;       // exact h-degree / fixed-level count BFS
+constexpr int kProfLevel1 = 1;    // level-1 lists
+constexpr int kProfLevelU = 2;    // level >= 2 lists (hashed union)
+constexpr int kProfFrontier = 3;  // removed-set ball hops, neighbour marking
+constexpr int kProfPeel = 4;      // min, select, finish, advance
+constexpr int kProfKinds = 5;
 
 struct DevState {
     unsigned long long c;        // current core value (max of round minima)
@@ -52,7 +62,10 @@ struct DevState {
     int nC[2];                   // changed-list sizes (sampled refresh, ping-pong)
     int work_ctr[4];             // dynamic scheduling counters
     unsigned long long updates;  // node recomputations
+    unsigned long long bytes[kProfKinds];  // algorithmic bytes per kernel class
     int err;                     // kErr* bits
+    int early;                   // exact early stop taken this round
+    int nH;                      // heavy nodes deferred by the level-1 kernel
     int pad;
 };
 
@@ -127,10 +140,24 @@ struct Graph {
     int32_t *queues;
     uint32_t *gbitmaps;
     int64_t scratch_ctas;
+    int32_t *listH;         // heavy nodes deferred by the level-1 warp kernel
     // last peel statistics
     int64_t last_rounds;
     int64_t last_updates;
     bool have_rounds;
+    // profiling: CUDA events around every launch of a kernel class
+    bool prof_on;
+    std::vector<cudaEvent_t>* ev_pool;
+    std::vector<int>* prof_kind;
+    std::vector<cudaEvent_t>* prof_ev;  // pairs (start, stop)
+    double prof_ms[kProfKinds];
+    int64_t prof_launches[kProfKinds];
+    // cached CUDA graph of a batch of peeling rounds
+    cudaGraphExec_t round_exec;
+    int round_exec_key[6];
+    int64_t round_exec_kernels;  // kernels in one replay of round_exec
+    // kernels launched on behalf of this graph (graph replays count their nodes)
+    int64_t launches;
 };
 }  // namespace kh
 
@@ -146,6 +173,10 @@ int ensure_work(Graph& g);
 int ensure_lists(Graph& g);
 int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps);
 int check_cuda(kh_ctx* ctx, cudaError_t e, const char* what);
+inline void count_launch(Graph& g, int64_t k) { g.launches += k; }
+// Profiling brackets around a launch (no-ops unless profiling is enabled).
+void prof_begin(Graph& g, int kind, cudaStream_t s);
+void prof_end(Graph& g, int kind, cudaStream_t s);
 }  // namespace kh
 
 #define KH_CUDA_TRY(ctx, expr)                                  \

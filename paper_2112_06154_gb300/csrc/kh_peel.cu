@@ -16,7 +16,12 @@
 // would still have d <= c when its turn came.
 //
 // Exact mode applies the paper's early stop (Sec. 5): once c >= |X| - 1 every
-// remaining node has deg_h <= |X| - 1 <= c, so all get core c in the next round.
+// remaining node has deg_h <= |X| - 1 <= c, so all get core c in the next
+// round; the refresh of this round is then skipped.
+//
+// A round reads every size it needs from device memory, so one captured CUDA
+// graph holds kRoundsPerGraph rounds; rounds that start with no alive node do
+// nothing.  The host replays the graph and reads the state once per replay.
 #include <cstring>
 
 #include "kh_internal.cuh"
@@ -27,10 +32,12 @@ namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kPeelThreads = 256;
+constexpr int kRoundsPerGraph = 8;
 
 template <typename T>
 __global__ void k_min_alive(const uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
                             DevState* st) {
+    if (st->n_alive == 0) return;
     unsigned long long m = ~0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
@@ -50,6 +57,7 @@ __global__ void k_min_alive(const uint8_t* __restrict__ alive, const T* __restri
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
             if (s_m[w] < m) m = s_m[w];
         if (m != ~0ull) atomicMin(&st->minval, m);
+        if (blockIdx.x == 0) atomicAdd(&st->bytes[kProfPeel], (unsigned long long)n * (1 + sizeof(T)));
     }
 }
 
@@ -57,6 +65,7 @@ template <typename T, typename C>
 __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
                          DevState* st, C* __restrict__ core, int32_t* __restrict__ round_of,
                          int32_t* __restrict__ R, int32_t* __restrict__ seen) {
+    if (st->n_alive == 0) return;
     const unsigned long long c = st->c > st->minval ? st->c : st->minval;
     const int round = st->round;
     const int lane = threadIdx.x & 31;
@@ -84,12 +93,23 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
     }
     for (int off = 16; off > 0; off >>= 1) keep += __shfl_down_sync(kFull, keep, off);
     if (lane == 0 && keep) atomicAdd(&st->n_alive_next, keep);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(&st->bytes[kProfPeel], (unsigned long long)n * (1 + sizeof(T)));
+}
+
+// Exact mode: decide the early stop (c >= |X_new| - 1) for this round.
+__global__ void k_early(DevState* st) {
+    if (st->n_alive == 0) return;
+    const unsigned long long c = st->c > st->minval ? st->c : st->minval;
+    const int left = st->n_alive_next;
+    st->early = (left > 0 && c + 1 >= (unsigned long long)left) ? 1 : 0;
 }
 
 // Early stop: every remaining node gets core c in round `round + 1`.
 template <typename C>
 __global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, const DevState* st,
                               C* __restrict__ core, int32_t* __restrict__ round_of) {
+    if (!st->early) return;
     const unsigned long long c = st->c > st->minval ? st->c : st->minval;
     const int round = st->round + 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -110,14 +130,16 @@ __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict_
 }
 
 __global__ void k_advance(DevState* st) {
+    if (st->n_alive == 0) return;
     if (st->minval > st->c && st->minval != ~0ull) st->c = st->minval;
     st->minval = ~0ull;
-    st->round += 1;
-    st->n_alive = st->n_alive_next;
+    st->round += st->early ? 2 : 1;
+    st->n_alive = st->early ? 0 : st->n_alive_next;
     st->n_alive_next = 0;
     st->nR = 0;
     st->nW = 0;
     st->nF[0] = st->nF[1] = 0;
+    st->early = 0;
 }
 
 int peel_grid(const Graph& g) {
@@ -137,24 +159,85 @@ int full_pass(Graph& g, bool sampled, cudaStream_t s) {
     return KH_OK;
 }
 
-int refresh(Graph& g, bool sampled, cudaStream_t s) {
+// One peeling round, entirely stream-ordered (capturable).
+int launch_round(Graph& g, bool sampled, cudaStream_t s) {
+    const int grid = peel_grid(g);
+    prof_begin(g, kProfPeel, s);
+    if (sampled) {
+        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state);
+        k_select<unsigned long long, unsigned long long><<<grid, kPeelThreads, 0, s>>>(
+            g.alive, g.d64, g.n, g.state, g.core64, g.round_of, g.listR, g.seen);
+        count_launch(g, 2);
+    } else {
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state);
+        k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
+            g.alive, g.d32, g.n, g.state, g.core32, g.round_of, g.listR, g.seen);
+        k_early<<<1, 1, 0, s>>>(g.state);
+        k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, g.core32,
+                                                             g.round_of);
+        count_launch(g, 4);
+    }
+    prof_end(g, kProfPeel, s);
+    int rc = KH_OK;
     if (!sampled) {
         for (int hop = 1; hop <= g.h; ++hop) launch_ball_hop(g, hop, s);
-        return launch_hdeg(g, g.listW, &g.state->nW, 0, g.d32, nullptr, 0, 0, s);
+        rc = launch_hdeg(g, g.listW, &g.state->nW, 0, g.d32, nullptr, 0, 0, s);
+    } else {
+        for (int i = 1; i <= g.h && rc == KH_OK; ++i) {
+            cudaMemsetAsync(&g.state->nW, 0, sizeof(int), s);
+            launch_mark_neighbours(g, g.listR, &g.state->nR, i, s);
+            if (i >= 2)
+                launch_mark_neighbours(g, g.listC[(i - 1) & 1], &g.state->nC[(i - 1) & 1], i, s);
+            rc = launch_level(g, i, g.listW, &g.state->nW, 0, i < g.h ? 1 : 0, s);
+        }
     }
-    for (int i = 1; i <= g.h; ++i) {
-        cudaMemsetAsync(&g.state->nW, 0, sizeof(int), s);
-        launch_mark_neighbours(g, g.listR, &g.state->nR, i, s);
-        if (i >= 2) launch_mark_neighbours(g, g.listC[(i - 1) & 1], &g.state->nC[(i - 1) & 1], i, s);
-        int rc = launch_level(g, i, g.listW, &g.state->nW, 0, i < g.h ? 1 : 0, s);
-        if (rc) return rc;
-    }
+    if (rc) return rc;
+    prof_begin(g, kProfPeel, s);
+    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state);
+    k_advance<<<1, 1, 0, s>>>(g.state);
+    count_launch(g, 2);
+    prof_end(g, kProfPeel, s);
     return KH_OK;
 }
 
 int check_state_err(Graph& g, const DevState& hs) {
     if (hs.err)
         return set_error(g.ctx, KH_EINTERNAL, "device check failed (flags 0x%x)", hs.err);
+    return KH_OK;
+}
+
+// Capture kRoundsPerGraph rounds into an executable graph (cached per shape).
+int round_graph(Graph& g, bool sampled, cudaStream_t s, cudaGraphExec_t* out) {
+    const int key[6] = {sampled ? 1 : 0, g.h, (int)g.M, (int)g.cap, (int)g.scratch_ctas, 1};
+    if (g.round_exec && memcmp(key, g.round_exec_key, sizeof(key)) == 0) {
+        *out = g.round_exec;
+        return KH_OK;
+    }
+    if (g.round_exec) {
+        cudaGraphExecDestroy(g.round_exec);
+        g.round_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    KH_CUDA_TRY(g.ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    int rc = KH_OK;
+    const int64_t before = g.launches;
+    for (int r = 0; r < kRoundsPerGraph && rc == KH_OK; ++r) rc = launch_round(g, sampled, s);
+    g.round_exec_kernels = g.launches - before;  // captured, not yet run
+    g.launches = before;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g.round_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.round_exec = nullptr;
+        return check_cuda(g.ctx, e, "cudaGraphInstantiate");
+    }
+    memcpy(g.round_exec_key, key, sizeof(key));
+    *out = g.round_exec;
     return KH_OK;
 }
 
@@ -167,13 +250,14 @@ int run_estimate_all(Graph& g) {
     rc = ensure_lists(g);
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
-    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.state, 0, sizeof(DevState), s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->err, 0, sizeof(int), s));
     rc = full_pass(g, true, s);
     if (rc) return rc;
-    DevState hs;
-    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&hs, g.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    int err = 0;
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&err, &g.state->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
-    return check_state_err(g, hs);
+    if (err) return set_error(g.ctx, KH_EINTERNAL, "device check failed (flags 0x%x)", err);
+    return KH_OK;
 }
 
 int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, bool out_dev) {
@@ -189,54 +273,46 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.seen, 0xff, sizeof(int32_t) * (size_t)g.n, s));
     DevState init;
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&init, g.state, sizeof(init), cudaMemcpyDeviceToHost, s));
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
+    unsigned long long keep_bytes[kProfKinds];
+    memcpy(keep_bytes, init.bytes, sizeof(keep_bytes));
     memset(&init, 0, sizeof(init));
+    memcpy(init.bytes, keep_bytes, sizeof(keep_bytes));  // profiling counters accumulate
     init.minval = ~0ull;
     init.n_alive = (int)g.n;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.state, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     rc = full_pass(g, sampled, s);
     if (rc) return rc;
-    const int grid = peel_grid(g);
+    // the BFS scratch must exist before capture (its allocation may synchronize)
     DevState hs;
-    int64_t rounds = 0;
-    int64_t alive_left = g.n;
-    while (alive_left > 0) {
-        if (rounds > g.n + 1)
-            return set_error(g.ctx, KH_ETIMEOUT, "peeling did not finish within n+1 rounds");
-        if (sampled) {
-            k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state);
-            k_select<unsigned long long, unsigned long long><<<grid, kPeelThreads, 0, s>>>(
-                g.alive, g.d64, g.n, g.state, g.core64, g.round_of, g.listR, g.seen);
+    int64_t launches = 0;
+    cudaGraphExec_t exec = nullptr;
+    const bool use_graph = !g.prof_on;
+    if (use_graph) {
+        rc = round_graph(g, sampled, s, &exec);
+        if (rc) return rc;
+    }
+    for (;;) {
+        if (use_graph) {
+            KH_CUDA_TRY(g.ctx, cudaGraphLaunch(exec, s));
+            launches += kRoundsPerGraph;
+            count_launch(g, g.round_exec_kernels);
         } else {
-            k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state);
-            k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
-                g.alive, g.d32, g.n, g.state, g.core32, g.round_of, g.listR, g.seen);
+            rc = launch_round(g, sampled, s);
+            if (rc) return rc;
+            launches += 1;
         }
         KH_CUDA_TRY(g.ctx, cudaGetLastError());
         KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&hs, g.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
         rc = check_state_err(g, hs);
         if (rc) return rc;
-        const unsigned long long c = hs.c > hs.minval ? hs.c : hs.minval;
-        alive_left = hs.n_alive_next;
-        ++rounds;
-        if (alive_left > 0 && !sampled && c + 1 >= (unsigned long long)alive_left) {
-            k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, g.core32,
-                                                                 g.round_of);
-            ++rounds;
-            alive_left = 0;
-        } else if (alive_left > 0) {
-            rc = refresh(g, sampled, s);
-            if (rc) return rc;
-        }
-        k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state);
-        k_advance<<<1, 1, 0, s>>>(g.state);
-        KH_CUDA_TRY(g.ctx, cudaGetLastError());
+        if (hs.n_alive == 0) break;
+        if (launches > g.n + 2 + kRoundsPerGraph)
+            return set_error(g.ctx, KH_ETIMEOUT, "peeling did not finish within n+1 rounds");
     }
-    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&hs, g.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
-    rc = check_state_err(g, hs);
-    if (rc) return rc;
-    g.last_rounds = rounds;
+    g.last_rounds = hs.round;
     g.last_updates = (int64_t)hs.updates;
     g.have_rounds = true;
     const size_t bytes = (size_t)g.n * (sampled ? sizeof(unsigned long long) : sizeof(int32_t));

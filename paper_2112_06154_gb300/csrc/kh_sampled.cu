@@ -58,10 +58,15 @@ struct LevelArgs {
     int track;
     int32_t* changed;
     int* n_changed;
+    int32_t* heavy;            // level 1: nodes of degree > kL1Heavy, for the CTA kernel
+    int* n_heavy;
     int* work_ctr;
     int* err;
     unsigned long long* updates;
+    unsigned long long* bytes;
 };
+
+constexpr int kL1Heavy = 512;
 
 __device__ __forceinline__ unsigned long long estimate_of(int S, int kappa, int rv, int64_t M) {
     // Alg. 1: d = |B[v,h] \ {v}| 2^k; if k > 0, d = max(d, M 2^(k-1))
@@ -85,18 +90,32 @@ __device__ __forceinline__ void record_change(const LevelArgs& a, int v, int S, 
     }
 }
 
+// Bytes a node's level-1 computation must move: row offsets, the row, the
+// neighbours' ranks, and the list it writes with its size and level.
+__device__ __forceinline__ unsigned long long level1_bytes(int64_t deg, int S, int last) {
+    return 8ull + 5ull * (unsigned long long)deg + (last ? 8ull : 4ull * (unsigned long long)S) + 5ull;
+}
+
 __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
     __shared__ int s_hist[kL1Threads / 32][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int* hist = s_hist[wib];
     const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_bytes = 0;
     for (int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < total; idx += nw) {
         const int v = a.worklist ? a.worklist[idx] : (int)idx;
         if (a.alive[v] != 1) continue;
+        const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+        if (e - b > kL1Heavy) {
+            if (lane == 0) {
+                const int p = atomicAdd(a.n_heavy, 1);
+                if (p < a.n) a.heavy[p] = v;
+            }
+            continue;
+        }
         hist[lane] = 0;
         __syncwarp();
-        const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
         for (int64_t k0 = b; k0 < e; k0 += 32) {
             const int64_t k = k0 + lane;
             if (k < e) {
@@ -117,6 +136,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
         const int kappa = over ? 32 - __clz(over) : 0;
         const int Sk = __shfl_sync(kFull, S, kappa & 31);
         const int Skap = kappa < 32 ? Sk : 0;
+        if (lane == 0) my_bytes += level1_bytes(e - b, Skap, a.last);
         if (a.last) {
             if (lane == 0) {
                 a.est[v] = estimate_of(Skap, kappa, rv, a.M);
@@ -155,6 +175,78 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
         }
         __syncwarp();
     }
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
+}
+
+// Level 1 for the nodes of degree > kL1Heavy deferred by k_level1: one CTA per node.
+__global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
+    __shared__ int s_hist[32];
+    __shared__ int s_kappa, s_S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nh = *a.n_heavy;
+    for (int idx = blockIdx.x; idx < nh; idx += gridDim.x) {
+        const int v = a.heavy[idx];
+        if (tid < 32) s_hist[tid] = 0;
+        __syncthreads();
+        const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
+        for (int64_t k = b + tid; k < e; k += blockDim.x) {
+            const int32_t u = a.col[k];
+            if (a.alive[u] == 1) atomicAdd(&s_hist[a.rank[u]], 1);
+        }
+        const int rv = a.rank[v];
+        if (tid == 0) atomicAdd(&s_hist[rv], 1);
+        __syncthreads();
+        if (tid < 32) {
+            int S = s_hist[lane];
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_down_sync(kFull, S, off);
+                if (lane + off < 32) S += t;
+            }
+            const uint32_t over = __ballot_sync(kFull, S > a.M);
+            const int kappa = over ? 32 - __clz(over) : 0;
+            const int Sk = __shfl_sync(kFull, S, kappa & 31);
+            const int above = __shfl_down_sync(kFull, S, 1);
+            s_hist[lane] = lane < 31 ? above : 0;
+            if (lane == 0) {
+                s_kappa = kappa;
+                s_S = kappa < 32 ? Sk : 0;
+            }
+        }
+        __syncthreads();
+        const int kappa = s_kappa, Skap = s_S;
+        if (a.last) {
+            if (tid == 0) {
+                a.est[v] = estimate_of(Skap, kappa, rv, a.M);
+                record_change(a, v, Skap, kappa);
+                atomicAdd(a.updates, 1ull);
+                atomicAdd(a.bytes, level1_bytes(e - b, Skap, 1));
+            }
+        } else {
+            uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
+            for (int64_t k = b + tid; k < e; k += blockDim.x) {
+                const int32_t u = a.col[k];
+                if (a.alive[u] == 1) {
+                    const int r = a.rank[u];
+                    if (r >= kappa) {
+                        const int p = atomicAdd(&s_hist[r], 1);
+                        if (p < a.cap) out[p] = ((uint32_t)r << kIdBits) | (uint32_t)u;
+                        else atomicOr(a.err, kErrList);
+                    }
+                }
+            }
+            if (tid == 0) {
+                if (rv >= kappa) {
+                    const int p = atomicAdd(&s_hist[rv], 1);
+                    if (p < a.cap) out[p] = ((uint32_t)rv << kIdBits) | (uint32_t)v;
+                    else atomicOr(a.err, kErrList);
+                }
+                record_change(a, v, Skap, kappa);
+                atomicAdd(a.bytes, level1_bytes(e - b, Skap, 0));
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // Insert `key` into the shared hash set; returns 1 if it was not there.
@@ -171,6 +263,9 @@ __device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, i
     return 0;
 }
 
+// Keys one thread loads per step (one 16-byte vector).
+constexpr int kKeysPerLane = 4;
+
 __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int hcap = 1 << lg;
@@ -178,8 +273,9 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     uint32_t* stage = s_dyn + hcap;  // hcap / 2 entries
     __shared__ int s_hist[32];
     __shared__ int s_src, s_t, s_entries, s_nstage, s_compact;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+    unsigned long long my_bytes = 0;
     for (;;) {
         if (tid == 0) s_src = atomicAdd(a.work_ctr, 1);
         __syncthreads();
@@ -215,13 +311,20 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             s_entries += 1;
         }
         __syncthreads();
-        // stream the neighbours' lists, one 32-key chunk per warp per step
-        int li = warp;  // neighbour index of this warp's current list
+        // G lanes share one neighbour list and read G*4 consecutive keys per
+        // step; G shrinks for high degree so that many lists are open at once
+        int G = 32;
+        while (G > 1 && (kLuThreads / G) < deg) G >>= 1;
+        const int ngroups = kLuThreads / G;
+        const int gid = tid / G, gl = tid % G;
+        const uint32_t gmask = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        const int step = kKeysPerLane * G;
+        int li = gid;  // neighbour index of this group's current list
         int pos = 0;
         bool any = true;
         while (any) {
             const int t = *(volatile int*)&s_t;
-            // advance to an alive neighbour with a non-empty list (warp-uniform)
+            // advance to an alive neighbour with a non-empty list (group-uniform)
             int32_t w = -1;
             int sz = 0;
             while (li < deg) {
@@ -230,27 +333,41 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                     sz = min(a.lsz_in[w], (int)a.cap);
                     if (sz > pos) break;
                 }
-                li += nwarps;
+                li += ngroups;
                 pos = 0;
             }
+            bool below = false;
             if (li < deg) {
-                const uint32_t* L = a.keys_in + (size_t)w * (size_t)a.cap;
-                const int p = pos + lane;
-                const bool valid = p < sz;
-                const uint32_t key = valid ? L[p] : 0u;
-                const int r = (int)(key >> kIdBits);
-                if (valid && r >= t) {
-                    if (set_insert(tab, lg, key, a.err)) {
-                        atomicAdd(&s_hist[r], 1);
-                        atomicAdd(&s_entries, 1);
+                const int p = pos + gl * kKeysPerLane;
+                if (p < sz) {
+                    const uint4 k4 =
+                        *reinterpret_cast<const uint4*>(a.keys_in + (size_t)w * (size_t)a.cap + p);
+                    const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+                    for (int q = 0; q < kKeysPerLane; ++q) {
+                        if (p + q < sz) {
+                            const uint32_t key = kk[q];
+                            const int r = (int)(key >> kIdBits);
+                            my_bytes += 4;
+                            if (r >= t) {
+                                if (set_insert(tab, lg, key, a.err)) {
+                                    atomicAdd(&s_hist[r], 1);
+                                    atomicAdd(&s_entries, 1);
+                                }
+                            } else {
+                                below = true;
+                            }
+                        }
                     }
                 }
-                const uint32_t below = __ballot_sync(kFull, valid && r < t);
-                if (below || pos + 32 >= sz) {
-                    li += nwarps;
+            }
+            const uint32_t bal = __ballot_sync(kFull, below);
+            if (li < deg) {
+                if ((bal & gmask) || pos + step >= sz) {
+                    li += ngroups;
                     pos = 0;
                 } else {
-                    pos += 32;
+                    pos += step;
                 }
             }
             any = __syncthreads_or(li < deg);
@@ -292,11 +409,13 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         int S = 0;
         for (int j = kappa; j < 32; ++j) S += s_hist[j];
         __syncthreads();
+        if (tid == 0) my_bytes += 8ull + 10ull * (unsigned long long)deg + 5ull;
         if (a.last) {
             if (tid == 0) {
                 a.est[v] = estimate_of(S, kappa, rv, a.M);
                 record_change(a, v, S, kappa);
                 atomicAdd(a.updates, 1ull);
+                my_bytes += 8;
             }
         } else {
             // write members grouped by rank, highest first
@@ -318,24 +437,31 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                     }
                 }
             }
-            if (tid == 0) record_change(a, v, S, kappa);
+            if (tid == 0) {
+                record_change(a, v, S, kappa);
+                my_bytes += 4ull * (unsigned long long)S;
+            }
         }
         __syncthreads();
     }
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
 __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                             const int32_t* __restrict__ list, const int* __restrict__ nlist,
                             int32_t* __restrict__ wl, int* nwl, const DevState* __restrict__ st,
-                            int phase, int64_t cap) {
+                            int phase, int64_t cap, unsigned long long* bytes) {
     const int lane = threadIdx.x & 31;
     const int nin = *nlist;
     const int stamp = st->round * kPhaseStride + phase;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_bytes = 0;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
         const int w = list[i];
         const int64_t b = rowptr[w], e = rowptr[w + 1];
+        if (lane == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
         for (int64_t k0 = b; k0 < e; k0 += 32) {
             const int64_t k = k0 + lane;
             bool isnew = false;
@@ -355,14 +481,15 @@ __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* _
             }
         }
     }
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 }  // namespace
 
 int table_lg(int64_t M) {
-    // capacity >= 2 (M + threads) rounded up to a power of two
+    // capacity >= 2 (M + keys inserted per step) rounded up to a power of two
     int lg = 10;
-    while ((int64_t(1) << lg) < 2 * (M + kLuThreads)) ++lg;
+    while ((int64_t(1) << lg) < 2 * (M + (int64_t)kKeysPerLane * kLuThreads)) ++lg;
     return lg;
 }
 
@@ -393,6 +520,8 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.track = track;
     a.changed = g.listC[level & 1];
     a.n_changed = &g.state->nC[level & 1];
+    a.heavy = g.listH;
+    a.n_heavy = &g.state->nH;
     a.work_ctr = &g.state->work_ctr[1];
     a.err = &g.state->err;
     a.updates = &g.state->updates;
@@ -403,13 +532,21 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     }
     const int64_t work = worklist ? g.n : count_static;
     if (level == 1) {
+        a.bytes = &g.state->bytes[kProfLevel1];
+        e = cudaMemsetAsync(a.n_heavy, 0, sizeof(int), s);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_heavy");
         int64_t grid = (work + (kL1Threads / 32) - 1) / (kL1Threads / 32);
         const int64_t gmax = (int64_t)g.ctx->sm_count * 8;
         if (grid > gmax) grid = gmax;
         if (grid < 1) grid = 1;
+        prof_begin(g, kProfLevel1, s);
         k_level1<<<(int)grid, kL1Threads, 0, s>>>(a);
+        k_level1_heavy<<<g.ctx->sm_count * 2, kL1Threads, 0, s>>>(a);
+        count_launch(g, 2);
+        prof_end(g, kProfLevel1, s);
         return KH_OK;
     }
+    a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
     const size_t dyn = (size_t)(1 << lg) * 4 + (size_t)(1 << (lg - 1)) * 4;
     e = cudaFuncSetAttribute(k_levelU, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -423,15 +560,22 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     if (grid < 1) grid = 1;
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    prof_begin(g, kProfLevelU, s);
     k_levelU<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
+    count_launch(g, 1);
+    prof_end(g, kProfLevelU, s);
     return KH_OK;
 }
 
 void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int phase,
                             cudaStream_t s) {
     const int grid = g.ctx->sm_count * 8;
+    prof_begin(g, kProfFrontier, s);
     k_mark_nbrs<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, list, d_count, g.listW,
-                                     &g.state->nW, g.state, phase, g.n);
+                                     &g.state->nW, g.state, phase, g.n,
+                                     &g.state->bytes[kProfFrontier]);
+    count_launch(g, 1);
+    prof_end(g, kProfFrontier, s);
 }
 
 }  // namespace kh

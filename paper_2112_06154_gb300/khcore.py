@@ -23,6 +23,13 @@ KH_ECUDA = -4
 KH_ETIMEOUT = -5
 KH_EINTERNAL = -6
 KH_DEVICE_PTR = 1
+KH_PROF_BFS = 0
+KH_PROF_LEVEL1 = 1
+KH_PROF_LEVELU = 2
+KH_PROF_FRONTIER = 3
+KH_PROF_PEEL = 4
+KH_PROF_KINDS = 5
+PROF_NAMES = ["bfs", "level1", "levelU", "frontier", "peel"]
 
 _ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",
              KH_ECUDA: "KH_ECUDA", KH_ETIMEOUT: "KH_ETIMEOUT", KH_EINTERNAL: "KH_EINTERNAL"}
@@ -49,6 +56,10 @@ SIGNATURES = [
     ("kh_core_exact", ctypes.c_int, [_P, _P, ctypes.c_uint32]),
     ("kh_core_sampled", ctypes.c_int, [_P, _P, ctypes.c_uint32]),
     ("kh_peel_info", ctypes.c_int, [_P, _P, _I64P, _I64P]),
+    ("kh_prof_enable", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("kh_prof_read", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _I64P,
+                                    ctypes.POINTER(ctypes.c_double)]),
+    ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_sync", ctypes.c_int, [_P]),
 ]
 
@@ -266,4 +277,24 @@ def kh_sync(g: Graph):
 def kh_graph_n(g: Graph) -> int:
     n = ctypes.c_int64()
     _check(load().kh_graph_n(g.handle, ctypes.byref(n)), g.ctx)
+    return int(n.value)
+
+
+def kh_prof_enable(g: Graph, on: bool = True):
+    _check(load().kh_prof_enable(g.handle, 1 if on else 0), g.ctx)
+
+
+def kh_prof_read(g: Graph, kind: int):
+    """(ms, launches, algorithmic bytes) accumulated for one kernel class."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    b = ctypes.c_double()
+    _check(load().kh_prof_read(g.handle, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
+           g.ctx)
+    return float(ms.value), int(n.value), float(b.value)
+
+
+def kh_launch_count(g: Graph) -> int:
+    n = ctypes.c_int64()
+    _check(load().kh_launch_count(g.handle, ctypes.byref(n)), g.ctx)
     return int(n.value)

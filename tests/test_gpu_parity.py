@@ -216,3 +216,27 @@ def test_parameter_errors(ctx):
     with pytest.raises(K.KhError):
         K.kh_sampled_counts(G, 5, 2)
     G.close()
+
+
+def test_profiled_rounds_match_graph_rounds(ctx):
+    """Profiling launches rounds one by one; results must equal graph replay."""
+    for sampled in (False, True):
+        G = load(ctx, CL20K, h=2, M=40)
+        fn = K.kh_core_sampled if sampled else K.kh_core_exact
+        a = fn(G)
+        _, ra, ua = K.kh_peel_info(G, False)
+        K.kh_prof_enable(G, True)
+        b = fn(G)
+        _, rb, ub = K.kh_peel_info(G, False)
+        assert (a == b).all() and ra == rb
+        total_ms = 0.0
+        for kind in range(K.KH_PROF_KINDS):
+            ms, n, byt = K.kh_prof_read(G, kind)
+            assert ms >= 0 and n >= 0 and byt >= 0
+            total_ms += ms
+        assert total_ms > 0
+        bfs = K.kh_prof_read(G, K.KH_PROF_BFS)
+        lvl = K.kh_prof_read(G, K.KH_PROF_LEVELU)
+        assert (bfs[1] > 0) != sampled and (lvl[1] > 0) == sampled
+        K.kh_prof_enable(G, False)
+        G.close()
