@@ -63,6 +63,10 @@ int ensure_work(Graph& g) {
     if ((rc = dalloc(g.ctx, &g.listC[0], n, "listC0"))) return rc;
     if ((rc = dalloc(g.ctx, &g.listC[1], n, "listC1"))) return rc;
     if ((rc = dalloc(g.ctx, &g.listH, n, "listH"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.fresh, n, "fresh"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.deadbm, ((n + 127) / 128) * 4, "deadbm"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.degX, n, "degX"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.lb64, n, "lb64"))) return rc;
     return KH_OK;
 }
 
@@ -192,6 +196,10 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.queues);
     dfree(&g.gbitmaps);
     dfree(&g.listH);
+    dfree(&g.fresh);
+    dfree(&g.deadbm);
+    dfree(&g.degX);
+    dfree(&g.lb64);
     if (g.round_exec) cudaGraphExecDestroy(g.round_exec);
     g.round_exec = nullptr;
     if (g.ev_pool) {
@@ -438,6 +446,7 @@ int kh_hdegree_exact(kh_graph* G, int32_t* deg, uint32_t flags) {
     int rc = kh::ensure_work(g);
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
     rc = kh::launch_hdeg(g, nullptr, nullptr, g.n, g.d32, nullptr, 0, 0, s);
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaGetLastError());
@@ -467,6 +476,7 @@ int kh_sampled_counts(kh_graph* G, int32_t j_lo, int32_t j_hi, int32_t* cnt, uin
         KH_CUDA_TRY(g.ctx, cudaMallocAsync((void**)&dcnt, sizeof(int32_t) * (size_t)g.n * nj, s));
     }
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
     rc = kh::launch_hdeg(g, nullptr, nullptr, g.n, g.d32, dcnt, j_lo, nj, s);
     if (rc == KH_OK && !(flags & KH_DEVICE_PTR) && g.n > 0) {
         rc = kh::copy_out(g, cnt, dcnt, sizeof(int32_t) * (size_t)g.n * nj, 0);

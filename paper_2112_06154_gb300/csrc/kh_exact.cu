@@ -99,16 +99,18 @@ struct BfsArgs {
     unsigned long long* updates;
     unsigned long long* bytes;  // algorithmic bytes: 8 + 4 deg per expanded vertex, 4 per result
     const int* skip;            // nonzero: the exact early stop fired, nothing to do
+    const uint32_t* deadbm;     // removed-node bitmap (shared-memory mode): seeds the visited set
 };
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
 // `valid` false for lanes past the end of the row).
-template <bool RANKS>
+template <bool RANKS, bool SEEDED>
 __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
                                       int* s_hist, bool valid, int32_t u, bool push, int lane,
                                       int& my) {
     bool isnew = false;
-    if (valid && a.alive[u] == 1) {
+    // seeded: removed nodes already have their bit set, no alive lookup needed
+    if (valid && (SEEDED || a.alive[u] == 1)) {
         const uint32_t bit = 1u << (u & 31);
         uint32_t* wp = bm + (u >> 5);
         if (!(*(volatile uint32_t*)wp & bit)) {
@@ -136,6 +138,27 @@ __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q
     }
 }
 
+// Expand the row [b, e): lanes take 32 consecutive entries, each warp step
+// issues four independent row loads before visiting (memory-level parallelism).
+template <bool RANKS, bool SEEDED>
+__device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
+                                           int* s_hist, int64_t b, int64_t e, int64_t first,
+                                           int64_t stride, bool push, int lane, int& my) {
+    for (int64_t k0 = b + first; k0 < e; k0 += stride) {
+        int32_t u[4];
+        bool val[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const int64_t k = k0 + qq * 32 + lane;
+            val[qq] = k < e;
+            u[qq] = val[qq] ? __ldg(a.col + k) : 0;
+        }
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq)
+            visit<RANKS, SEEDED>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, lane, my);
+    }
+}
+
 template <bool RANKS, bool SMEM>
 __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     extern __shared__ __align__(16) uint32_t s_bm_dyn[];
@@ -149,8 +172,11 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     if (total == 0) return;
     unsigned long long my_bytes = 0;
 
-    for (int i = tid; i < a.words; i += blockDim.x) bm[i] = 0u;
-    __syncthreads();
+    const bool seeded = SMEM && a.deadbm != nullptr;
+    if (!seeded) {
+        for (int i = tid; i < a.words; i += blockDim.x) bm[i] = 0u;
+        __syncthreads();
+    }
 
     for (;;) {
         if (tid == 0) s_src = atomicAdd(a.work_ctr, 1);
@@ -163,6 +189,15 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             if (RANKS && tid < a.nj) a.cnt[(size_t)v * a.nj + tid] = 0;
             __syncthreads();
             continue;
+        }
+        if (seeded) {
+            // visited set := removed nodes (vector copy of the dead bitmap)
+            const uint4* src = reinterpret_cast<const uint4*>(a.deadbm);
+            uint4* dst = reinterpret_cast<uint4*>(bm);
+            const int w4 = a.words >> 2;
+            for (int i = tid; i < w4; i += blockDim.x) dst[i] = __ldg(src + i);
+            for (int i = (w4 << 2) + tid; i < a.words; i += blockDim.x) bm[i] = __ldg(a.deadbm + i);
+            __syncthreads();
         }
         if (tid == 0) {
             q[0] = v;
@@ -193,24 +228,22 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                         continue;
                     }
                 }
-                for (int64_t k0 = b; k0 < e; k0 += 32) {
-                    const int64_t k = k0 + lane;
-                    const bool valid = k < e;
-                    const int32_t u = valid ? a.col[k] : 0;
-                    visit<RANKS>(a, bm, q, &s_qtail, s_hist, valid, u, push, lane, my);
-                }
+                if (seeded)
+                    expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my);
+                else
+                    expand_row<RANKS, false>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my);
             }
             __syncthreads();
             const int nh = min(s_nheavy, kMaxHeavy);
             for (int hi = 0; hi < nh; ++hi) {
                 const int w = s_heavy[hi];
                 const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
-                for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
-                    const int64_t k = k0 + lane;
-                    const bool valid = k < e;
-                    const int32_t u = valid ? a.col[k] : 0;
-                    visit<RANKS>(a, bm, q, &s_qtail, s_hist, valid, u, push, lane, my);
-                }
+                if (seeded)
+                    expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
+                                            4 * blockDim.x, push, lane, my);
+                else
+                    expand_row<RANKS, false>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
+                                             4 * blockDim.x, push, lane, my);
             }
             __syncthreads();
             fs = fe;
@@ -231,8 +264,9 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             for (int j = a.jlo + tid; j < 32; ++j) c += s_hist[j];
             a.cnt[(size_t)v * a.nj + tid] = c;
         }
-        // clear the visited set for the next source
-        if (SMEM) {
+        // clear the visited set for the next source (seeded sets are re-copied)
+        if (seeded) {
+        } else if (SMEM) {
             uint4* b4 = reinterpret_cast<uint4*>(bm);
             const int w4 = a.words >> 2;
             for (int i = tid; i < w4; i += blockDim.x) b4[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -249,34 +283,38 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
 
 // One hop of the ball around the removed set R in the OLD graph (alive != 0):
 // every newly reached vertex joins the next frontier (if more hops follow) and,
-// when it is still alive (alive == 1), the recompute work list.
+// when it is still alive (alive == 1), the recompute work list.  One CTA per
+// frontier vertex, so a hub's row is spread over all of the CTA's warps.
 __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                            const int32_t* __restrict__ fin, const int* __restrict__ nfin,
                            int32_t* __restrict__ fout, int* nfout, int32_t* __restrict__ wl, int* nwl,
                            const DevState* __restrict__ st, int push_next, int64_t cap,
-                           unsigned long long* bytes) {
+                           unsigned long long* bytes, int32_t* __restrict__ degX) {
     if (st->early) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nin = *nfin;
-    unsigned long long my_bytes = 0;
     const int stamp = st->round * kPhaseStride;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
+    unsigned long long my_bytes = 0;
+    for (int64_t i = blockIdx.x; i < nin; i += gridDim.x) {
         const int w = fin[i];
         const int64_t b = rowptr[w], e = rowptr[w + 1];
-        if (lane == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
-        for (int64_t k0 = b; k0 < e; k0 += 32) {
+        if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
+        for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
             const int64_t k = k0 + lane;
             bool isnew = false;
             int32_t u = 0;
+            uint8_t au = 0;
             if (k < e) {
                 u = col[k];
-                if (alive[u] != 0 && *(volatile int32_t*)(seen + u) != stamp)
+                au = alive[u];
+                // hop 1 scans each removed node's row once: alive neighbours lose a degree
+                if (degX && au == 1) atomicSub(degX + u, 1);
+                if (au != 0 && *(volatile int32_t*)(seen + u) != stamp)
                     isnew = atomicExch(seen + u, stamp) != stamp;
             }
             const bool to_f = isnew && push_next;
-            const bool to_w = isnew && alive[u] == 1;
+            const bool to_w = isnew && au == 1;
             uint32_t m1 = __ballot_sync(kFull, to_f);
             uint32_t m2 = __ballot_sync(kFull, to_w);
             int b1 = 0, b2 = 0;
@@ -297,7 +335,48 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
             }
         }
     }
-    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+}
+
+// Mark nodes stale and give each the lower bound max(deg_X(v), max_w deg_X(w))
+// of deg_h(v; X), h >= 2: N(v; h) contains N(w; 1) for every alive neighbour w.
+// The bound only depends on the 2-ball of v, which the h-ball refresh covers.
+// One CTA per node (hub rows are spread over the CTA).
+__global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const uint8_t* __restrict__ alive, const int32_t* __restrict__ degX,
+                              const int32_t* __restrict__ list, const int* __restrict__ nlist,
+                              int64_t n, uint8_t* __restrict__ fresh,
+                              unsigned long long* __restrict__ lb, const DevState* __restrict__ st,
+                              unsigned long long* bytes, int h) {
+    if (st->early) return;
+    __shared__ int s_max[kBfsThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cnt = list ? (int64_t)(*nlist) : n;
+    unsigned long long my_bytes = 0;
+    for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int v = list ? list[i] : (int)i;
+        if (alive[v] != 1) continue;  // block-uniform
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        int m = 0;
+        if (h >= 2) {
+            for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+                const int32_t w = col[k];
+                if (alive[w] == 1) m = max(m, degX[w]);
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_down_sync(kFull, m, off));
+        if (lane == 0) s_max[warp] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
+            // h = 1: deg_1 = deg_X(v) itself; the neighbour term needs h >= 2
+            lb[v] = (unsigned long long)max(m, degX[v]);
+            fresh[v] = 0;
+            my_bytes += 8ull + 5ull * (unsigned long long)(e - b) + 13ull;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 int pick_grid(int sm, int per_sm, int64_t work) {
@@ -369,6 +448,7 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.updates = &g.state->updates;
     a.bytes = &g.state->bytes[kProfBfs];
     a.skip = worklist ? &g.state->early : nullptr;
+    a.deadbm = g.deadbm;
     e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
     prof_begin(g, kProfBfs, s);
@@ -389,7 +469,18 @@ void launch_ball_hop(Graph& g, int hop, cudaStream_t s) {
     prof_begin(g, kProfFrontier, s);
     k_ball_hop<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, fin, nfin, fout, nfout,
                                     g.listW, &g.state->nW, g.state, hop < g.h ? 1 : 0, g.n,
-                                    &g.state->bytes[kProfFrontier]);
+                                    &g.state->bytes[kProfFrontier], hop == 1 ? g.degX : nullptr);
+    count_launch(g, 1);
+    prof_end(g, kProfFrontier, s);
+}
+
+void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStream_t s) {
+    if (g.n == 0) return;
+    const int grid = g.ctx->sm_count * 8;
+    prof_begin(g, kProfFrontier, s);
+    k_stale_exact<<<grid, kBfsThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.degX, list, d_count, g.n,
+                                       g.fresh, g.lb64, g.state, &g.state->bytes[kProfFrontier],
+                                       g.h);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

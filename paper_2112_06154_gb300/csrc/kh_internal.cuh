@@ -66,7 +66,8 @@ struct DevState {
     int err;                     // kErr* bits
     int early;                   // exact early stop taken this round
     int nH;                      // heavy nodes deferred by the level-1 kernel
-    int pad;
+    int nQ;                      // refine list size (stale nodes due this round)
+    unsigned long long minU;     // min of the upper bounds d over alive nodes
 };
 
 struct Graph;
@@ -80,6 +81,9 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
                 int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s);
 // one hop of the removed set's ball in the old graph (exact refresh)
 void launch_ball_hop(Graph& g, int hop, cudaStream_t s);
+// exact mode: mark the nodes of `list` (nullptr: all) stale and set their
+// lower bound max(deg_X(v), max_w deg_X(w)) <= deg_h(v; X) for h >= 2
+void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStream_t s);
 
 // ---- launchers (kh_sampled.cu) -----------------------------------------------
 // level i of the list recursion for `count` nodes (worklist == nullptr: all);
@@ -89,6 +93,9 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
 // neighbours (alive) of the nodes in `list` join the work list, deduplicated by stamp phase
 void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int phase,
                             cudaStream_t s);
+// sampled mode: mark the nodes of `list` (nullptr: all) stale at the last
+// level with a lower bound of their estimate
+void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s);
 
 // ---- launchers (kh_peel.cu) --------------------------------------------------
 int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, bool out_dev);
@@ -141,6 +148,13 @@ struct Graph {
     uint32_t *gbitmaps;
     int64_t scratch_ctas;
     int32_t *listH;         // heavy nodes deferred by the level-1 warp kernel
+    // lazy refinement of the last level: fresh[v] = d[v] is exact for the
+    // current alive set; otherwise d[v] is an upper bound (d never grows as
+    // nodes leave) and lb64[v] (exact mode) a lower bound
+    uint8_t *fresh;
+    uint32_t *deadbm;       // bitmap of removed nodes (n bits), seeds BFS visited sets
+    int32_t *degX;          // alive degree (exact mode)
+    unsigned long long *lb64;
     // last peel statistics
     int64_t last_rounds;
     int64_t last_updates;

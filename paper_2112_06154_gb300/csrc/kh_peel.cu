@@ -19,6 +19,20 @@
 // remaining node has deg_h <= |X| - 1 <= c, so all get core c in the next
 // round; the refresh of this round is then skipped.
 //
+// Lazy last level.  A node whose h-neighbourhood may have changed is only
+// marked stale: its last value stays as an upper bound (d never grows as X
+// shrinks) and it carries a lower bound lb (exact: max(deg_X(v), max_w
+// deg_X(w)); sampled: Alg. 1 on its own level-(h-1) list, a sub-list of
+// N(v; h) with v first, so Prop. 4.2 applies).  Each round first takes
+// U = min over alive d (upper bounds), recomputes every stale node with
+// lb <= T = max(c, U), and only then takes the minimum and the removal set:
+// the true minimum is at most U <= T, every skipped node has d >= lb > T,
+// so the minimum is attained by a fresh node and no skipped node can have
+// d <= c' = max(c, min) <= T.  The result is the same core map, with the
+// expensive recomputations of high-degree nodes deferred until c nears them
+// (the lower-bound pruning of the exact baselines, and the paper's lazy
+// initialisation, Sec. 5).
+//
 // A round reads every size it needs from device memory, so one captured CUDA
 // graph holds kRoundsPerGraph rounds; rounds that start with no alive node do
 // nothing.  The host replays the graph and reads the state once per replay.
@@ -36,7 +50,7 @@ constexpr int kRoundsPerGraph = 8;
 
 template <typename T>
 __global__ void k_min_alive(const uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
-                            DevState* st) {
+                            DevState* st, unsigned long long* target) {
     if (st->n_alive == 0) return;
     unsigned long long m = ~0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -56,8 +70,63 @@ __global__ void k_min_alive(const uint8_t* __restrict__ alive, const T* __restri
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
             if (s_m[w] < m) m = s_m[w];
-        if (m != ~0ull) atomicMin(&st->minval, m);
+        if (m != ~0ull) atomicMin(target, m);
         if (blockIdx.x == 0) atomicAdd(&st->bytes[kProfPeel], (unsigned long long)n * (1 + sizeof(T)));
+    }
+}
+
+struct LbArgs {
+    const unsigned long long* lb;  // lower bounds of stale nodes
+};
+
+__device__ __forceinline__ unsigned long long lower_bound(const LbArgs& a, int v) { return a.lb[v]; }
+
+__global__ void k_min_lb(const uint8_t* __restrict__ alive, const uint8_t* __restrict__ fresh,
+                         int64_t n, LbArgs a, DevState* st) {
+    if (st->n_alive == 0) return;
+    unsigned long long m = ~0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (alive[v] == 1 && !fresh[v]) {
+            const unsigned long long x = lower_bound(a, (int)v);
+            if (x < m) m = x;
+        }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_down_sync(kFull, m, off);
+        if (o < m) m = o;
+    }
+    if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(&st->minU, m);
+}
+
+// Stale nodes with lb <= T = max(c, U) join the refine list and become fresh
+// (their value is recomputed right after, before anything reads it).
+__global__ void k_collect(const uint8_t* __restrict__ alive, uint8_t* __restrict__ fresh, int64_t n,
+                          LbArgs a, DevState* st, int32_t* __restrict__ out) {
+    if (st->n_alive == 0) return;
+    const unsigned long long T = st->c > st->minU ? st->c : st->minU;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nround = (n + 31) & ~(int64_t)31;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
+        bool due = false;
+        if (v < n && alive[v] == 1 && !fresh[v]) due = lower_bound(a, (int)v) <= T;
+        const uint32_t m = __ballot_sync(kFull, due);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&st->nQ, __popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (due) {
+            out[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+            fresh[v] = 1;
+        }
+    }
+}
+
+__global__ void k_init_exact(const int64_t* __restrict__ rowptr, int64_t n, int32_t* __restrict__ degX,
+                             int32_t* __restrict__ d) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        degX[v] = (int32_t)(rowptr[v + 1] - rowptr[v]);
+        d[v] = 0x7fffffff;  // no upper bound known yet
     }
 }
 
@@ -122,11 +191,14 @@ __global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, const DevS
 }
 
 __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict__ R,
-                         const DevState* st) {
+                         const DevState* st, uint32_t* __restrict__ deadbm) {
     const int nR = st->nR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nR; i += stride)
-        alive[R[i]] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nR; i += stride) {
+        const int v = R[i];
+        alive[v] = 0;
+        atomicOr(deadbm + (v >> 5), 1u << (v & 31));
+    }
 }
 
 __global__ void k_advance(DevState* st) {
@@ -140,6 +212,8 @@ __global__ void k_advance(DevState* st) {
     st->nW = 0;
     st->nF[0] = st->nF[1] = 0;
     st->early = 0;
+    st->nQ = 0;
+    st->minU = ~0ull;
 }
 
 int peel_grid(const Graph& g) {
@@ -149,27 +223,77 @@ int peel_grid(const Graph& g) {
     return (int)(grid < 1 ? 1 : grid);
 }
 
-// Full-graph pass: every alive node gets d (exact deg_h or the estimate).
-int full_pass(Graph& g, bool sampled, cudaStream_t s) {
-    if (!sampled) return launch_hdeg(g, nullptr, nullptr, g.n, g.d32, nullptr, 0, 0, s);
-    for (int i = 1; i <= g.h; ++i) {
-        int rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s);
+LbArgs lb_args(const Graph& g) {
+    LbArgs a;
+    a.lb = g.lb64;
+    return a;
+}
+
+// Recompute the last level of the refine list (stale nodes with lb <= T).
+int refine(Graph& g, bool sampled, cudaStream_t s) {
+    const int grid = peel_grid(g);
+    const LbArgs la = lb_args(g);
+    prof_begin(g, kProfPeel, s);
+    k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state, g.listB);
+    count_launch(g, 1);
+    prof_end(g, kProfPeel, s);
+    if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s);
+    return launch_hdeg(g, g.listB, &g.state->nQ, 0, g.d32, nullptr, 0, 0, s);
+}
+
+// Start of a peel: levels below h in full (sampled), every node stale with its
+// lower bound, then the nodes of smallest lower bound get exact values.
+int start_peel(Graph& g, bool sampled, cudaStream_t s) {
+    const int grid = peel_grid(g);
+    int rc = KH_OK;
+    if (sampled) {
+        for (int i = 1; i < g.h && rc == KH_OK; ++i) rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s);
         if (rc) return rc;
+        KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.d64, 0xff, sizeof(unsigned long long) * (size_t)g.n, s));
+        launch_stale_sampled(g, nullptr, nullptr, s);
+    } else {
+        k_init_exact<<<grid, kPeelThreads, 0, s>>>(g.rowptr, g.n, g.degX, g.d32);
+        count_launch(g, 1);
+        launch_stale_exact(g, nullptr, nullptr, s);
     }
+    const LbArgs la = lb_args(g);
+    k_min_lb<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state);
+    count_launch(g, 1);
+    rc = refine(g, sampled, s);
+    if (rc) return rc;
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->nQ, 0, sizeof(int), s));
+    const unsigned long long all1 = ~0ull;
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&g.state->minU, &all1, sizeof(all1), cudaMemcpyHostToDevice, s));
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // keeps `all1` alive until copied
     return KH_OK;
 }
 
 // One peeling round, entirely stream-ordered (capturable).
 int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     const int grid = peel_grid(g);
+    int rc = KH_OK;
+    // U = min of the upper bounds; refine stale nodes with lb <= max(c, U)
+    prof_begin(g, kProfPeel, s);
+    if (sampled)
+        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
+                                                                      &g.state->minU);
+    else
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state,
+                                                           &g.state->minU);
+    count_launch(g, 1);
+    prof_end(g, kProfPeel, s);
+    rc = refine(g, sampled, s);
+    if (rc) return rc;
     prof_begin(g, kProfPeel, s);
     if (sampled) {
-        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state);
+        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
+                                                                      &g.state->minval);
         k_select<unsigned long long, unsigned long long><<<grid, kPeelThreads, 0, s>>>(
             g.alive, g.d64, g.n, g.state, g.core64, g.round_of, g.listR, g.seen);
         count_launch(g, 2);
     } else {
-        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state);
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state,
+                                                           &g.state->minval);
         k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
             g.alive, g.d32, g.n, g.state, g.core32, g.round_of, g.listR, g.seen);
         k_early<<<1, 1, 0, s>>>(g.state);
@@ -178,22 +302,29 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
         count_launch(g, 4);
     }
     prof_end(g, kProfPeel, s);
-    int rc = KH_OK;
     if (!sampled) {
+        // the ball of R in the old graph: alive degrees drop (hop 1), the
+        // nodes within h hops become stale with new lower bounds
         for (int hop = 1; hop <= g.h; ++hop) launch_ball_hop(g, hop, s);
-        rc = launch_hdeg(g, g.listW, &g.state->nW, 0, g.d32, nullptr, 0, 0, s);
+        launch_stale_exact(g, g.listW, &g.state->nW, s);
     } else {
-        for (int i = 1; i <= g.h && rc == KH_OK; ++i) {
+        for (int i = 1; i < g.h && rc == KH_OK; ++i) {
             cudaMemsetAsync(&g.state->nW, 0, sizeof(int), s);
             launch_mark_neighbours(g, g.listR, &g.state->nR, i, s);
             if (i >= 2)
                 launch_mark_neighbours(g, g.listC[(i - 1) & 1], &g.state->nC[(i - 1) & 1], i, s);
-            rc = launch_level(g, i, g.listW, &g.state->nW, 0, i < g.h ? 1 : 0, s);
+            rc = launch_level(g, i, g.listW, &g.state->nW, 0, 1, s);
         }
+        if (rc) return rc;
+        // the last level of A(R) and of A(changed at h-1) becomes stale
+        cudaMemsetAsync(&g.state->nW, 0, sizeof(int), s);
+        launch_mark_neighbours(g, g.listR, &g.state->nR, g.h, s);
+        if (g.h >= 2)
+            launch_mark_neighbours(g, g.listC[(g.h - 1) & 1], &g.state->nC[(g.h - 1) & 1], g.h, s);
+        launch_stale_sampled(g, g.listW, &g.state->nW, s);
     }
-    if (rc) return rc;
     prof_begin(g, kProfPeel, s);
-    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state);
+    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm);
     k_advance<<<1, 1, 0, s>>>(g.state);
     count_launch(g, 2);
     prof_end(g, kProfPeel, s);
@@ -251,7 +382,7 @@ int run_estimate_all(Graph& g) {
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->err, 0, sizeof(int), s));
-    rc = full_pass(g, true, s);
+    for (int i = 1; i <= g.h && rc == KH_OK; ++i) rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s);
     if (rc) return rc;
     int err = 0;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&err, &g.state->err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -272,6 +403,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     g.have_rounds = false;
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.seen, 0xff, sizeof(int32_t) * (size_t)g.n, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
     DevState init;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&init, g.state, sizeof(init), cudaMemcpyDeviceToHost, s));
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
@@ -280,9 +412,11 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     memset(&init, 0, sizeof(init));
     memcpy(init.bytes, keep_bytes, sizeof(keep_bytes));  // profiling counters accumulate
     init.minval = ~0ull;
+    init.minU = ~0ull;
     init.n_alive = (int)g.n;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.state, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-    rc = full_pass(g, sampled, s);
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // `init` is a host stack object
+    rc = start_peel(g, sampled, s);
     if (rc) return rc;
     // the BFS scratch must exist before capture (its allocation may synchronize)
     DevState hs;

@@ -249,33 +249,45 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
     }
 }
 
-// Insert `key` into the shared hash set; returns 1 if it was not there.
+// Insert `key` into the shared hash set; returns its slot if it was not
+// there, -1 if it was (or the probe limit was reached).
 __device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, int* err) {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t s = ((key & kIdMask) * 0x9E3779B1u) >> (32 - lg);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const uint32_t prev = atomicCAS(tab + s, kEmpty, key);
-        if (prev == kEmpty) return 1;
-        if (prev == key) return 0;
+        if (prev == kEmpty) return (int)s;
+        if (prev == key) return -1;
         s = (s + 1u) & mask;
     }
     atomicOr(err, kErrProbe);
-    return 0;
+    return -1;
 }
 
 // Keys one thread loads per step (one 16-byte vector).
 constexpr int kKeysPerLane = 4;
 
+// Shared memory of k_levelU for a table of 2^lg slots: keys, compaction
+// stage (half size), and the list of used slots (16-bit indices).
+size_t levelU_smem(int lg) {
+    const size_t hcap = (size_t)1 << lg;
+    return hcap * 4 + (hcap >> 1) * 4 + hcap * 2;
+}
+
 __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int hcap = 1 << lg;
     uint32_t* tab = s_dyn;
-    uint32_t* stage = s_dyn + hcap;  // hcap / 2 entries
+    uint32_t* stage = s_dyn + hcap;                                        // hcap / 2 keys
+    uint16_t* used = reinterpret_cast<uint16_t*>(s_dyn + hcap + (hcap >> 1));  // hcap slots
     __shared__ int s_hist[32];
-    __shared__ int s_src, s_t, s_entries, s_nstage, s_compact;
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+    if (total == 0) return;
     unsigned long long my_bytes = 0;
+    // the table starts empty once per launch; every node leaves it empty again
+    for (int i = tid; i < hcap; i += blockDim.x) tab[i] = kEmpty;
     for (;;) {
         if (tid == 0) s_src = atomicAdd(a.work_ctr, 1);
         __syncthreads();
@@ -286,11 +298,10 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             __syncthreads();
             continue;
         }
-        for (int i = tid; i < hcap; i += blockDim.x) tab[i] = kEmpty;
         if (tid < 32) s_hist[tid] = 0;
         if (tid == 0) {
             s_t = 0;
-            s_entries = 0;
+            s_nused = 0;
         }
         __syncthreads();
         const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
@@ -306,9 +317,11 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         __syncthreads();
         const int rv = a.rank[v];
         if (tid == 0 && rv >= s_t) {
-            set_insert(tab, lg, ((uint32_t)rv << kIdBits) | (uint32_t)v, a.err);
-            s_hist[rv] += 1;
-            s_entries += 1;
+            const int slot = set_insert(tab, lg, ((uint32_t)rv << kIdBits) | (uint32_t)v, a.err);
+            if (slot >= 0) {
+                used[s_nused++] = (uint16_t)slot;
+                s_hist[rv] += 1;
+            }
         }
         __syncthreads();
         // G lanes share one neighbour list and read G*4 consecutive keys per
@@ -350,9 +363,12 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                             const int r = (int)(key >> kIdBits);
                             my_bytes += 4;
                             if (r >= t) {
-                                if (set_insert(tab, lg, key, a.err)) {
+                                const int slot = set_insert(tab, lg, key, a.err);
+                                if (slot >= 0) {
+                                    const int u = atomicAdd(&s_nused, 1);
+                                    if (u < hcap) used[u] = (uint16_t)slot;
+                                    else atomicOr(a.err, kErrProbe);
                                     atomicAdd(&s_hist[r], 1);
-                                    atomicAdd(&s_entries, 1);
                                 }
                             } else {
                                 below = true;
@@ -371,41 +387,50 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
             }
             any = __syncthreads_or(li < deg);
-            if (tid == 0) {
-                // smallest level >= t with at most M distinct members
-                int S = 0, tn = s_t;
-                for (int j = 31; j >= s_t; --j) {
-                    S += s_hist[j];
-                    if (S > a.M) {
-                        tn = j + 1;
-                        break;
-                    }
+            if (warp == 0) {
+                // smallest level >= t with at most M distinct members (Alg. 5's
+                // trim): lane j holds S_j = #{distinct keys with rank >= j}
+                int S = s_hist[lane];
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int x = __shfl_down_sync(kFull, S, off);
+                    if (lane + off < 32) S += x;
                 }
-                s_t = tn;
-                s_compact = s_entries > (hcap >> 1);
-                s_nstage = 0;
+                const uint32_t over = __ballot_sync(kFull, S > a.M);
+                const int pmax = over ? 31 - __clz(over) : -1;
+                if (lane == 0) {
+                    const int told = s_t;
+                    s_t = max(told, pmax + 1);
+                    s_compact = s_nused > (hcap >> 1);
+                    s_nstage = 0;
+                }
             }
             __syncthreads();
             if (s_compact) {
-                const int tc = s_t;
-                for (int i = tid; i < hcap; i += blockDim.x) {
-                    const uint32_t key = tab[i];
-                    if (key != kEmpty && (int)(key >> kIdBits) >= tc) {
+                // drop keys below t: empty their slots, re-insert the rest
+                const int tc = s_t, nu = min(s_nused, hcap);
+                for (int i = tid; i < nu; i += blockDim.x) {
+                    const int slot = used[i];
+                    const uint32_t key = tab[slot];
+                    tab[slot] = kEmpty;
+                    if ((int)(key >> kIdBits) >= tc) {
                         const int p = atomicAdd(&s_nstage, 1);
                         if (p < (hcap >> 1)) stage[p] = key;
                         else atomicOr(a.err, kErrProbe);
                     }
                 }
                 __syncthreads();
-                for (int i = tid; i < hcap; i += blockDim.x) tab[i] = kEmpty;
+                if (tid == 0) s_nused = 0;
                 __syncthreads();
                 const int ns = min(s_nstage, hcap >> 1);
-                for (int i = tid; i < ns; i += blockDim.x) set_insert(tab, lg, stage[i], a.err);
-                if (tid == 0) s_entries = ns;
+                for (int i = tid; i < ns; i += blockDim.x) {
+                    const int slot = set_insert(tab, lg, stage[i], a.err);
+                    if (slot >= 0) used[atomicAdd(&s_nused, 1)] = (uint16_t)slot;
+                }
                 __syncthreads();
             }
         }
         const int kappa = s_t;
+        const int nu = min(s_nused, hcap);
         int S = 0;
         for (int j = kappa; j < 32; ++j) S += s_hist[j];
         __syncthreads();
@@ -417,8 +442,9 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 atomicAdd(a.updates, 1ull);
                 my_bytes += 8;
             }
+            for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
         } else {
-            // write members grouped by rank, highest first
+            // write members grouped by rank, highest first, emptying the table
             if (tid < 32) {
                 int above = 0;
                 for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
@@ -426,15 +452,15 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             }
             __syncthreads();
             uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
-            for (int i = tid; i < hcap; i += blockDim.x) {
-                const uint32_t key = tab[i];
-                if (key != kEmpty) {
-                    const int r = (int)(key >> kIdBits);
-                    if (r >= kappa) {
-                        const int p = atomicAdd(&s_hist[r], 1);
-                        if (p < a.cap) out[p] = key;
-                        else atomicOr(a.err, kErrList);
-                    }
+            for (int i = tid; i < nu; i += blockDim.x) {
+                const int slot = used[i];
+                const uint32_t key = tab[slot];
+                tab[slot] = kEmpty;
+                const int r = (int)(key >> kIdBits);
+                if (r >= kappa) {
+                    const int p = atomicAdd(&s_hist[r], 1);
+                    if (p < a.cap) out[p] = key;
+                    else atomicOr(a.err, kErrList);
                 }
             }
             if (tid == 0) {
@@ -448,21 +474,22 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
+// Alive neighbours of the listed nodes join the work list once per stamp
+// (round, phase).  One CTA per listed node.
 __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                             const int32_t* __restrict__ list, const int* __restrict__ nlist,
                             int32_t* __restrict__ wl, int* nwl, const DevState* __restrict__ st,
                             int phase, int64_t cap, unsigned long long* bytes) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nin = *nlist;
     const int stamp = st->round * kPhaseStride + phase;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_bytes = 0;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
+    for (int64_t i = blockIdx.x; i < nin; i += gridDim.x) {
         const int w = list[i];
         const int64_t b = rowptr[w], e = rowptr[w + 1];
-        if (lane == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
-        for (int64_t k0 = b; k0 < e; k0 += 32) {
+        if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
+        for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
             const int64_t k = k0 + lane;
             bool isnew = false;
             int32_t u = 0;
@@ -481,7 +508,71 @@ __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* _
             }
         }
     }
-    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+}
+
+// Alg. 1 on a level list of size S and level kappa, with the node of rank
+// r_first counted first (it is a member of the list's neighbourhood).
+__device__ __forceinline__ unsigned long long est_first(int S, int kappa, int r_first, int64_t M) {
+    const int T = S - (r_first >= kappa ? 1 : 0);
+    unsigned long long d = (unsigned long long)T << kappa;
+    if (kappa > 0) {
+        const unsigned long long f = (unsigned long long)M << (kappa - 1);
+        if (f > d) d = f;
+    }
+    return d;
+}
+
+// Mark nodes stale at the last level h and give each a lower bound of its
+// estimate: N(v; h-1) and, for every alive neighbour w, N(w; h-1) (which
+// contains v) are inside N(v; h); Alg. 1 on either with v's rank first is at
+// most the estimate of N(v; h) (Prop. 4.2).  Only the level-(h-1) sizes and
+// levels are read.  One CTA per node.
+__global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const uint8_t* __restrict__ alive, const uint8_t* __restrict__ rank,
+                                const int32_t* __restrict__ lsz_prev, const uint8_t* __restrict__ lk_prev,
+                                int64_t M, const int32_t* __restrict__ list, const int* __restrict__ nlist,
+                                int64_t n, uint8_t* __restrict__ fresh,
+                                unsigned long long* __restrict__ lb, unsigned long long* bytes) {
+    __shared__ unsigned long long s_max[kLuThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cnt = list ? (int64_t)(*nlist) : n;
+    unsigned long long my_bytes = 0;
+    for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int v = list ? list[i] : (int)i;
+        if (alive[v] != 1) continue;  // block-uniform
+        unsigned long long m = 0;
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        if (lsz_prev) {
+            const int rv = rank[v];
+            for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+                const int32_t w = col[k];
+                if (alive[w] == 1) {
+                    const unsigned long long x = est_first(lsz_prev[w], lk_prev[w], rv, M);
+                    if (x > m) m = x;
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_down_sync(kFull, m, off);
+                if (o > m) m = o;
+            }
+            if (lane == 0) s_max[warp] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                    if (s_max[w] > m) m = s_max[w];
+                const unsigned long long own = est_first(lsz_prev[v], lk_prev[v], rv, M);
+                if (own > m) m = own;
+            }
+        }
+        if (threadIdx.x == 0) {
+            lb[v] = m;
+            fresh[v] = 0;
+            my_bytes += 29ull + 9ull * (unsigned long long)(e - b);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 }  // namespace
@@ -548,7 +639,7 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     }
     a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
-    const size_t dyn = (size_t)(1 << lg) * 4 + (size_t)(1 << (lg - 1)) * 4;
+    const size_t dyn = levelU_smem(lg);
     e = cudaFuncSetAttribute(k_levelU, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
     int per_sm = 0;
@@ -574,6 +665,19 @@ void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int p
     k_mark_nbrs<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, list, d_count, g.listW,
                                      &g.state->nW, g.state, phase, g.n,
                                      &g.state->bytes[kProfFrontier]);
+    count_launch(g, 1);
+    prof_end(g, kProfFrontier, s);
+}
+
+void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s) {
+    if (g.n == 0) return;
+    const int grid = g.ctx->sm_count * 8;
+    const int32_t* lsz_prev = g.h >= 2 ? g.lsz + (size_t)(g.h - 2) * g.n : nullptr;
+    const uint8_t* lk_prev = g.h >= 2 ? g.lk + (size_t)(g.h - 2) * g.n : nullptr;
+    prof_begin(g, kProfFrontier, s);
+    k_stale_sampled<<<grid, kLuThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.rank, lsz_prev, lk_prev, g.M,
+                                         list, d_count, g.n, g.fresh, g.lb64,
+                                         &g.state->bytes[kProfFrontier]);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

@@ -240,3 +240,39 @@ def test_profiled_rounds_match_graph_rounds(ctx):
         assert (bfs[1] > 0) != sampled and (lvl[1] > 0) == sampled
         K.kh_prof_enable(G, False)
         G.close()
+
+
+FAMILIES = {
+    "ba": gg.barabasi_albert(1500, 4, 31),
+    "grid_shortcuts": gg.grid(50, 60, 0.01, 32),
+    "cl_dense": gg.chung_lu(1200, 25, 2.1, 300, 33),
+    "rmat": gg.rmat(11, 8, 0.57, 0.19, 0.19, 34),
+}
+
+
+@pytest.mark.parametrize("family", sorted(FAMILIES))
+@pytest.mark.parametrize("h", [2, 3])
+def test_core_exact_families(ctx, family, h):
+    g = FAMILIES[family]
+    G = load(ctx, g, h=h)
+    core = K.kh_core_exact(G)
+    want, wround, steps = O.core_exact(*g, h)
+    assert (core == want).all()
+    ro, rounds, _ = K.kh_peel_info(G)
+    assert rounds == steps and (ro == wround).all()
+    G.close()
+
+
+@pytest.mark.parametrize("family", sorted(FAMILIES))
+@pytest.mark.parametrize("h,M", [(2, 20), (3, 12), (4, 30)])
+def test_core_sampled_families(ctx, family, h, M):
+    g = FAMILIES[family]
+    n = g[0].size - 1
+    G = load(ctx, g, h=h, M=M)
+    core = K.kh_core_sampled(G)
+    r = O.ranks(n, 1)
+    want, wround, steps = O.core_sampled(*g, r, h, M)
+    assert (core == want).all()
+    ro, rounds, _ = K.kh_peel_info(G)
+    assert rounds == steps and (ro == wround).all()
+    G.close()
