@@ -10,6 +10,7 @@
 // lone frontier vertex) are expanded by the whole CTA.  New vertices are
 // appended to the CTA's queue with one warp-aggregated atomic per warp step.
 #include <cstdio>
+#include <cstring>
 
 #include "kh_internal.cuh"
 
@@ -104,13 +105,14 @@ struct BfsArgs {
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
 // `valid` false for lanes past the end of the row).
-template <bool RANKS, bool SEEDED>
+template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
 __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
                                       int* s_hist, bool valid, int32_t u, bool push, int lane,
                                       int& my) {
     bool isnew = false;
-    // seeded: removed nodes already have their bit set, no alive lookup needed
-    if (valid && (SEEDED || a.alive[u] == 1)) {
+    // seeded: removed nodes already have their bit set, no alive lookup needed;
+    // ALLALIVE: the whole graph, no alive array at all
+    if (valid && (SEEDED || ALLALIVE || a.alive[u] == 1)) {
         const uint32_t bit = 1u << (u & 31);
         uint32_t* wp = bm + (u >> 5);
         if (!(*(volatile uint32_t*)wp & bit)) {
@@ -140,7 +142,7 @@ __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q
 
 // Expand the row [b, e): lanes take 32 consecutive entries, each warp step
 // issues four independent row loads before visiting (memory-level parallelism).
-template <bool RANKS, bool SEEDED>
+template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
 __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
                                            int* s_hist, int64_t b, int64_t e, int64_t first,
                                            int64_t stride, bool push, int lane, int& my) {
@@ -155,11 +157,11 @@ __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32
         }
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq)
-            visit<RANKS, SEEDED>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, lane, my);
+            visit<RANKS, SEEDED, ALLALIVE>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, lane, my);
     }
 }
 
-template <bool RANKS, bool SMEM>
+template <bool RANKS, bool SMEM, bool ALLALIVE = false>
 __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     extern __shared__ __align__(16) uint32_t s_bm_dyn[];
     __shared__ int s_src, s_qtail, s_count, s_nheavy;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
         const int64_t idx = s_src;
         if (idx >= total) break;
         const int v = a.worklist ? a.worklist[idx] : (int)idx;
-        if (a.alive[v] != 1) {
+        if (!ALLALIVE && a.alive[v] != 1) {
             if (tid == 0) a.deg[v] = 0;
             if (RANKS && tid < a.nj) a.cnt[(size_t)v * a.nj + tid] = 0;
             __syncthreads();
@@ -231,7 +233,8 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 if (seeded)
                     expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my);
                 else
-                    expand_row<RANKS, false>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my);
+                    expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push,
+                                                       lane, my);
             }
             __syncthreads();
             const int nh = min(s_nheavy, kMaxHeavy);
@@ -242,8 +245,8 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                     expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
                                             4 * blockDim.x, push, lane, my);
                 else
-                    expand_row<RANKS, false>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
-                                             4 * blockDim.x, push, lane, my);
+                    expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
+                                                       4 * blockDim.x, push, lane, my);
             }
             __syncthreads();
             fs = fe;
@@ -485,4 +488,101 @@ void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStrea
     prof_end(g, kProfFrontier, s);
 }
 
+// ---------------------------------------------------------------------------
+// Exact h-degrees without any allocation
+//
+// Some callers cannot allocate device memory: a serving process whose device
+// memory is carved up once at start-up by its own pool, code enqueueing work
+// while a stream is being captured into a CUDA graph (where cudaMalloc is not
+// allowed), or a real-time caller that must not block on the allocator.  This
+// variant of the BFS kernel runs on caller-owned inputs and outputs and keeps
+// its scratch (work counter and the per-CTA BFS queues) in one file-scope
+// device array of fixed size, which every GPU that loads the library holds
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocScratchInts = (int64_t)16 << 20;  // 64 MiB per device
+constexpr int64_t kNoAllocHeaderInts = 64;                  // counters, 256-byte aligned
+constexpr int kNoAllocMaxDevices = 64;
+// the shared-memory visited bitmap bounds n: words * 4 <= kSmemBitmapMax
+constexpr int64_t kNoAllocMaxN = (kSmemBitmapMax / 4) * 32;
+
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocScratchInts];
+// host-side: the device address of g_noalloc_scratch on each device, looked
+// up once per device (the symbol itself is only a host stand-in)
+int32_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
 }  // namespace kh
+
+extern "C" int kh_hdegree_exact_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                        int32_t h, int32_t* deg, void* cuda_stream) {
+    using namespace kh;
+    if (n < 0 || h < 1 || h > kMaxH) return KH_EINVAL;
+    if (n > kNoAllocMaxN) return KH_EINVAL;
+    if (n == 0) return KH_OK;
+    if (!rowptr || !col || !deg) return KH_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return KH_ECUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return KH_EINVAL;
+    if (!g_noalloc_addr[dev]) {
+        // first call on this device (with it current): find the array's address
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return KH_ECUDA;
+        }
+        g_noalloc_addr[dev] = (int32_t*)p;
+    }
+    int32_t* base = g_noalloc_addr[dev];
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int sm = 0;
+    if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return KH_ECUDA;
+    }
+    const int words = (int)((n + 31) / 32);
+    const size_t dyn = (size_t)((((int64_t)words + 3) & ~(int64_t)3) * 4);
+    void (*kern)(BfsArgs) = k_hdeg<false, true, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return KH_ECUDA;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBfsThreads, dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return KH_ECUDA;
+    }
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm * per_sm;
+    const int64_t fit = (kNoAllocScratchInts - kNoAllocHeaderInts) / n;  // queues of n entries
+    if (grid > fit) grid = fit;
+    if (grid > n) grid = n;
+    BfsArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rowptr = rowptr;
+    a.col = col;
+    a.n = n;
+    a.h = h;
+    a.words = words;
+    a.count_static = n;
+    a.deg = deg;
+    a.queues = base + kNoAllocHeaderInts;
+    a.qcap = n;
+    a.work_ctr = base;
+    a.err = base + 1;
+    a.updates = reinterpret_cast<unsigned long long*>(base + 4);
+    a.bytes = reinterpret_cast<unsigned long long*>(base + 6);
+    // the counters must start at zero; the queues need no clearing
+    if (cudaMemsetAsync(base, 0, kNoAllocHeaderInts * sizeof(int32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return KH_ECUDA;
+    }
+    kern<<<(int)grid, kBfsThreads, dyn, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return KH_ECUDA;
+    return KH_OK;
+}

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("kh_prof_read", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _I64P,
                                     ctypes.POINTER(ctypes.c_double)]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
+    ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
     ("kh_sync", ctypes.c_int, [_P]),
 ]
 
@@ -298,3 +299,17 @@ def kh_launch_count(g: Graph) -> int:
     n = ctypes.c_int64()
     _check(load().kh_launch_count(g.handle, ctypes.byref(n)), g.ctx)
     return int(n.value)
+
+
+def kh_hdegree_exact_noalloc(rowptr, col, h: int, deg, stream=None) -> int:
+    """Allocation-free exact h-degrees on device tensors (see include/khcore.h).
+
+    rowptr int64[n+1], col int32[nnz] and deg int32[n] are CUDA tensors of
+    the current device; returns the C return code (0 on success)."""
+    n = int(rowptr.shape[0]) - 1
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return int(load().kh_hdegree_exact_noalloc(n, ctypes.c_void_p(rowptr.data_ptr()),
+                                               ctypes.c_void_p(col.data_ptr()), h,
+                                               ctypes.c_void_p(deg.data_ptr()), s))
