@@ -115,26 +115,29 @@ def budget_M(n: int, eps: float, delta: float) -> int:
 
 def hball(rowptr, col, v: int, h: int, alive=None) -> np.ndarray:
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     out = np.zeros(max(n, 1), dtype=np.int32)
     dist = np.full(max(n, 1), -1, dtype=np.int32)
-    s = _load().kho_hball(n, _p(rowptr), _p(col), _p(_alive(alive, n)), v, h, _p(out), _p(dist))
+    s = _load().kho_hball(n, _p(rowptr), _p(col), _p(al), v, h, _p(out), _p(dist))
     return out[:s].copy()
 
 
 def hdegree_exact(rowptr, col, h: int, alive=None) -> np.ndarray:
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     deg = np.zeros(max(n, 1), dtype=np.int32)
-    _check(_load().kho_hdegree_exact(n, _p(rowptr), _p(col), _p(_alive(alive, n)), h, _p(deg)),
+    _check(_load().kho_hdegree_exact(n, _p(rowptr), _p(col), _p(al), h, _p(deg)),
            "hdegree_exact")
     return deg[:n]
 
 
 def fixed_counts(rowptr, col, r, h: int, jlo: int, jhi: int, alive=None) -> np.ndarray:
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     r = np.ascontiguousarray(r, dtype=np.uint8)
     nj = jhi - jlo + 1
     cnt = np.zeros((max(n, 1), nj), dtype=np.int32)
-    _check(_load().kho_fixed_counts(n, _p(rowptr), _p(col), _p(_alive(alive, n)), _p(r), h,
+    _check(_load().kho_fixed_counts(n, _p(rowptr), _p(col), _p(al), _p(r), h,
                                     jlo, jhi, _p(cnt)), "fixed_counts")
     return cnt[:n]
 
@@ -142,11 +145,12 @@ def fixed_counts(rowptr, col, r, h: int, jlo: int, jhi: int, alive=None) -> np.n
 def estimate_def(rowptr, col, r, h: int, M: int, alive=None):
     """(est uint64[n], k uint8[n], bsize int32[n]) from Def. 4.1 on N(v;h,X)."""
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     r = np.ascontiguousarray(r, dtype=np.uint8)
     est = np.zeros(max(n, 1), dtype=np.uint64)
     k = np.zeros(max(n, 1), dtype=np.uint8)
     bs = np.zeros(max(n, 1), dtype=np.int32)
-    _check(_load().kho_estimate_def(n, _p(rowptr), _p(col), _p(_alive(alive, n)), _p(r), h, M,
+    _check(_load().kho_estimate_def(n, _p(rowptr), _p(col), _p(al), _p(r), h, M,
                                     _p(est), _p(k), _p(bs)), "estimate_def")
     return est[:n], k[:n], bs[:n]
 
@@ -154,13 +158,14 @@ def estimate_def(rowptr, col, r, h: int, M: int, alive=None):
 def estimate_dp(rowptr, col, r, h: int, M: int, alive=None, levels: bool = False):
     """(est, k, bsize[, level_size int32[n,h], level_k uint8[n,h]]) via Alg. 2 levels."""
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     r = np.ascontiguousarray(r, dtype=np.uint8)
     est = np.zeros(max(n, 1), dtype=np.uint64)
     k = np.zeros(max(n, 1), dtype=np.uint8)
     bs = np.zeros(max(n, 1), dtype=np.int32)
     ls = np.zeros((max(n, 1), h), dtype=np.int32) if levels else None
     lk = np.zeros((max(n, 1), h), dtype=np.uint8) if levels else None
-    _check(_load().kho_estimate_dp(n, _p(rowptr), _p(col), _p(_alive(alive, n)), _p(r), h, M,
+    _check(_load().kho_estimate_dp(n, _p(rowptr), _p(col), _p(al), _p(r), h, M,
                                    _p(est), _p(k), _p(bs), _p(ls), _p(lk)), "estimate_dp")
     if levels:
         return est[:n], k[:n], bs[:n], ls[:n], lk[:n]
@@ -191,9 +196,10 @@ def core_sampled(rowptr, col, r, h: int, M: int, mode: int = 0):
 def hdegree_some(rowptr, col, h: int, vertices, alive=None) -> np.ndarray:
     """deg_h(v; X) for the listed nodes only."""
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     vs = np.ascontiguousarray(vertices, dtype=np.int32)
     deg = np.zeros(max(vs.size, 1), dtype=np.int32)
-    _check(_load().kho_hdegree_some(n, _p(rowptr), _p(col), _p(_alive(alive, n)), h, _p(vs),
+    _check(_load().kho_hdegree_some(n, _p(rowptr), _p(col), _p(al), h, _p(vs),
                                     vs.size, _p(deg)), "hdegree_some")
     return deg[:vs.size]
 
@@ -201,13 +207,14 @@ def hdegree_some(rowptr, col, h: int, vertices, alive=None) -> np.ndarray:
 def estimate_def_some(rowptr, col, r, h: int, M: int, vertices, alive=None):
     """Def. 4.1 (est, k, bsize) for the listed nodes only."""
     rowptr, col, n = _graph(rowptr, col)
+    al = _alive(alive, n)  # held until the C call returns
     r = np.ascontiguousarray(r, dtype=np.uint8)
     vs = np.ascontiguousarray(vertices, dtype=np.int32)
     m = max(vs.size, 1)
     est = np.zeros(m, dtype=np.uint64)
     k = np.zeros(m, dtype=np.uint8)
     bs = np.zeros(m, dtype=np.int32)
-    _check(_load().kho_estimate_def_some(n, _p(rowptr), _p(col), _p(_alive(alive, n)), _p(r), h, M,
+    _check(_load().kho_estimate_def_some(n, _p(rowptr), _p(col), _p(al), _p(r), h, M,
                                          _p(vs), vs.size, _p(est), _p(k), _p(bs)),
            "estimate_def_some")
     return est[:vs.size], k[:vs.size], bs[:vs.size]
