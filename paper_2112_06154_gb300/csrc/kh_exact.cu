@@ -405,7 +405,7 @@ void launch_validate(const Graph& g, int* d_err, cudaStream_t s) {
 }
 
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
-                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s) {
+                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s, int* round_ctr) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
     const int words = (int)((g.n + 31) / 32);
@@ -446,14 +446,16 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.queues = g.queues;
     a.qcap = g.n;
     a.gbitmaps = g.gbitmaps;
-    a.work_ctr = &g.state->work_ctr[0];
+    a.work_ctr = round_ctr ? round_ctr : &g.state->work_ctr[0];
     a.err = &g.state->err;
     a.updates = &g.state->updates;
     a.bytes = &g.state->bytes[kProfBfs];
     a.skip = worklist ? &g.state->early : nullptr;
     a.deadbm = g.deadbm;
-    e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
-    if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    if (!round_ctr) {
+        e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    }
     prof_begin(g, kProfBfs, s);
     kern<<<grid, kBfsThreads, dyn, s>>>(a);
     count_launch(g, 1);
@@ -464,14 +466,13 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
 void launch_ball_hop(Graph& g, int hop, cudaStream_t s) {
     // hop 1 starts from R; hop k >= 2 from the frontier written by hop k-1
     const int32_t* fin = hop == 1 ? g.listR : (hop & 1 ? g.listB : g.listA);
-    const int* nfin = hop == 1 ? &g.state->nR : &g.state->nF[(hop - 1) & 1];
+    const int* nfin = hop == 1 ? &g.state->nR : &g.state->rc[kRcF + hop - 1];
     int32_t* fout = hop & 1 ? g.listA : g.listB;
-    int* nfout = &g.state->nF[hop & 1];
-    cudaMemsetAsync(nfout, 0, sizeof(int), s);
+    int* nfout = &g.state->rc[kRcF + hop];
     const int grid = g.ctx->sm_count * 8;
     prof_begin(g, kProfFrontier, s);
     k_ball_hop<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, fin, nfin, fout, nfout,
-                                    g.listW, &g.state->nW, g.state, hop < g.h ? 1 : 0, g.n,
+                                    g.listW, &g.state->rc[kRcW], g.state, hop < g.h ? 1 : 0, g.n,
                                     &g.state->bytes[kProfFrontier], hop == 1 ? g.degX : nullptr);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);

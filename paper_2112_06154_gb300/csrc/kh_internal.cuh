@@ -50,6 +50,19 @@ constexpr int kProfFrontier = 3;  // removed-set ball hops, neighbour marking
 constexpr int kProfPeel = 4;      // min, select, finish, advance
 constexpr int kProfKinds = 5;
 
+// Per-round counters: every launch inside a peeling round has its own slot,
+// and the last block of the round's final kernel zeroes them all, so a round
+// needs no memset nodes.
+constexpr int kRcBfs = 0;          // refine BFS work counter
+constexpr int kRcRefineWork = 1;   // refine last-level list work counter
+constexpr int kRcRefineHeavy = 2;  // refine level-1 heavy count (h = 1)
+constexpr int kRcLevelWork = 3;    // + i: refresh level i work counter, i = 1..kMaxH
+constexpr int kRcLevelHeavy = 20;  // + i: refresh level i heavy count
+constexpr int kRcW = 37;           // + i: work list of level i (0: exact affected nodes)
+constexpr int kRcF = 54;           // + hop: frontier written by that hop (exact)
+constexpr int kRcC = 71;           // + i: changed nodes at level i
+constexpr int kRcCount = 88;
+
 struct DevState {
     unsigned long long c;        // current core value (max of round minima)
     unsigned long long minval;   // min d over alive nodes in this round
@@ -57,9 +70,7 @@ struct DevState {
     int n_alive;                 // alive nodes at the start of the round
     int n_alive_next;            // alive nodes after this round's removal
     int nR;                      // |R| removed this round
-    int nF[2];                   // frontier sizes (exact refresh)
-    int nW;                      // work-list size
-    int nC[2];                   // changed-list sizes (sampled refresh, ping-pong)
+    int nC[2];                   // changed-list sizes (standalone level passes)
     int work_ctr[4];             // dynamic scheduling counters
     unsigned long long updates;  // node recomputations
     unsigned long long bytes[kProfKinds];  // algorithmic bytes per kernel class
@@ -68,6 +79,8 @@ struct DevState {
     int nH;                      // heavy nodes deferred by the level-1 kernel
     int nQ;                      // refine list size (stale nodes due this round)
     unsigned long long minU;     // min of the upper bounds d over alive nodes
+    int rc[kRcCount];            // per-round counters (kRc*)
+    int done;                    // blocks of the round's final kernel that finished
 };
 
 struct Graph;
@@ -78,7 +91,8 @@ void launch_validate(const Graph& g, int* d_err, cudaStream_t s);
 // exact h-degrees of `count` nodes (worklist == nullptr: nodes 0..n-1) into deg32;
 // when cnt != nullptr also the fixed-level counts for j in [jlo, jlo+nj).
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
-                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s);
+                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
+                int* round_ctr = nullptr);
 // one hop of the removed set's ball in the old graph (exact refresh)
 void launch_ball_hop(Graph& g, int hop, cudaStream_t s);
 // exact mode: mark the nodes of `list` (nullptr: all) stale and set their
@@ -88,11 +102,15 @@ void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStrea
 // ---- launchers (kh_sampled.cu) -----------------------------------------------
 // level i of the list recursion for `count` nodes (worklist == nullptr: all);
 // track != 0 records nodes whose (|B|, k) changed into the changed list.
+// round_mode 0: standalone (counters zeroed with memsets); 1: refresh of
+// level `level` inside a round; 2: refine of the last level inside a round
+// (per-round counters, no memsets).
 int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
-                 int64_t count_static, int track, cudaStream_t s);
-// neighbours (alive) of the nodes in `list` join the work list, deduplicated by stamp phase
-void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int phase,
-                            cudaStream_t s);
+                 int64_t count_static, int track, cudaStream_t s, int round_mode = 0);
+// alive neighbours of the nodes in list1 and list2 (may be nullptr) join the
+// work list listW (count *out_count), deduplicated by stamp phase
+void launch_mark_neighbours(Graph& g, const int* list1, const int* cnt1, const int* list2,
+                            const int* cnt2, int phase, int* out_count, cudaStream_t s);
 // sampled mode: mark the nodes of `list` (nullptr: all) stale at the last
 // level with a lower bound of their estimate
 void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s);

@@ -9,7 +9,7 @@
 //               then a bounded BFS per such node;
 //      sampled: level i = 1..h recomputes the alive neighbours of R and of the
 //               nodes whose (|B|, k) changed at level i-1 (Alg. 3).
-//   4. alive[R] = 0, counters advance                      (k_finish, k_advance)
+//   4. alive[R] = 0; the last block advances the state          (k_finish)
 // Removing every node with d <= c at once gives the same core map as Alg. 4's
 // one-at-a-time loop because d(v; X) never grows as X shrinks (deg_h by
 // inclusion of neighbourhoods; the estimate by Prop. 4.2): every node of R
@@ -166,20 +166,18 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
         atomicAdd(&st->bytes[kProfPeel], (unsigned long long)n * (1 + sizeof(T)));
 }
 
-// Exact mode: decide the early stop (c >= |X_new| - 1) for this round.
-__global__ void k_early(DevState* st) {
+// Exact mode early stop: when c >= |X_new| - 1 every remaining node gets core
+// c in round `round + 1`.  Every block evaluates the condition; block 0
+// records it for the kernels that follow (they skip the refresh).
+template <typename C>
+__global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* st,
+                              C* __restrict__ core, int32_t* __restrict__ round_of) {
     if (st->n_alive == 0) return;
     const unsigned long long c = st->c > st->minval ? st->c : st->minval;
     const int left = st->n_alive_next;
-    st->early = (left > 0 && c + 1 >= (unsigned long long)left) ? 1 : 0;
-}
-
-// Early stop: every remaining node gets core c in round `round + 1`.
-template <typename C>
-__global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, const DevState* st,
-                              C* __restrict__ core, int32_t* __restrict__ round_of) {
-    if (!st->early) return;
-    const unsigned long long c = st->c > st->minval ? st->c : st->minval;
+    const bool early = left > 0 && c + 1 >= (unsigned long long)left;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->early = early ? 1 : 0;
+    if (!early) return;
     const int round = st->round + 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
@@ -190,8 +188,11 @@ __global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, const DevS
         }
 }
 
-__global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict__ R,
-                         const DevState* st, uint32_t* __restrict__ deadbm) {
+// Ends a round: removed nodes leave (alive = 0, dead bitmap bit set); the
+// last block to finish advances the state and zeroes the per-round counters.
+__global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict__ R, DevState* st,
+                         uint32_t* __restrict__ deadbm) {
+    __shared__ int s_last;
     const int nR = st->nR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nR; i += stride) {
@@ -199,21 +200,29 @@ __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict_
         alive[v] = 0;
         atomicOr(deadbm + (v >> 5), 1u << (v & 31));
     }
-}
-
-__global__ void k_advance(DevState* st) {
-    if (st->n_alive == 0) return;
-    if (st->minval > st->c && st->minval != ~0ull) st->c = st->minval;
-    st->minval = ~0ull;
-    st->round += st->early ? 2 : 1;
-    st->n_alive = st->early ? 0 : st->n_alive_next;
-    st->n_alive_next = 0;
-    st->nR = 0;
-    st->nW = 0;
-    st->nF[0] = st->nF[1] = 0;
-    st->early = 0;
-    st->nQ = 0;
-    st->minU = ~0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < kRcCount; i += blockDim.x) st->rc[i] = 0;
+    if (threadIdx.x == 0) {
+        if (st->n_alive != 0) {
+            if (st->minval > st->c && st->minval != ~0ull) st->c = st->minval;
+            st->round += st->early ? 2 : 1;
+            st->n_alive = st->early ? 0 : st->n_alive_next;
+        }
+        st->minval = ~0ull;
+        st->minU = ~0ull;
+        st->n_alive_next = 0;
+        st->nR = 0;
+        st->nQ = 0;
+        st->early = 0;
+        st->done = 0;
+    }
 }
 
 int peel_grid(const Graph& g) {
@@ -237,8 +246,9 @@ int refine(Graph& g, bool sampled, cudaStream_t s) {
     k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state, g.listB);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
-    if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s);
-    return launch_hdeg(g, g.listB, &g.state->nQ, 0, g.d32, nullptr, 0, 0, s);
+    if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s, 2);
+    return launch_hdeg(g, g.listB, &g.state->nQ, 0, g.d32, nullptr, 0, 0, s,
+                       &g.state->rc[kRcBfs]);
 }
 
 // Start of a peel: levels below h in full (sampled), every node stale with its
@@ -261,6 +271,8 @@ int start_peel(Graph& g, bool sampled, cudaStream_t s) {
     count_launch(g, 1);
     rc = refine(g, sampled, s);
     if (rc) return rc;
+    // the bootstrap used the per-round counters: zero them for round 0
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.state->rc, 0, sizeof(int) * kRcCount, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->nQ, 0, sizeof(int), s));
     const unsigned long long all1 = ~0ull;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&g.state->minU, &all1, sizeof(all1), cudaMemcpyHostToDevice, s));
@@ -296,37 +308,33 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
                                                            &g.state->minval);
         k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
             g.alive, g.d32, g.n, g.state, g.core32, g.round_of, g.listR, g.seen);
-        k_early<<<1, 1, 0, s>>>(g.state);
         k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, g.core32,
                                                              g.round_of);
-        count_launch(g, 4);
+        count_launch(g, 3);
     }
     prof_end(g, kProfPeel, s);
     if (!sampled) {
         // the ball of R in the old graph: alive degrees drop (hop 1), the
         // nodes within h hops become stale with new lower bounds
         for (int hop = 1; hop <= g.h; ++hop) launch_ball_hop(g, hop, s);
-        launch_stale_exact(g, g.listW, &g.state->nW, s);
+        launch_stale_exact(g, g.listW, &g.state->rc[kRcW], s);
     } else {
+        int* rcs = g.state->rc;
         for (int i = 1; i < g.h && rc == KH_OK; ++i) {
-            cudaMemsetAsync(&g.state->nW, 0, sizeof(int), s);
-            launch_mark_neighbours(g, g.listR, &g.state->nR, i, s);
-            if (i >= 2)
-                launch_mark_neighbours(g, g.listC[(i - 1) & 1], &g.state->nC[(i - 1) & 1], i, s);
-            rc = launch_level(g, i, g.listW, &g.state->nW, 0, 1, s);
+            // level i: A(R), plus A(nodes changed at level i-1)
+            launch_mark_neighbours(g, g.listR, &g.state->nR, i >= 2 ? g.listC[(i - 1) & 1] : nullptr,
+                                   rcs + kRcC + i - 1, i, rcs + kRcW + i, s);
+            rc = launch_level(g, i, g.listW, rcs + kRcW + i, 0, 1, s, 1);
         }
         if (rc) return rc;
         // the last level of A(R) and of A(changed at h-1) becomes stale
-        cudaMemsetAsync(&g.state->nW, 0, sizeof(int), s);
-        launch_mark_neighbours(g, g.listR, &g.state->nR, g.h, s);
-        if (g.h >= 2)
-            launch_mark_neighbours(g, g.listC[(g.h - 1) & 1], &g.state->nC[(g.h - 1) & 1], g.h, s);
-        launch_stale_sampled(g, g.listW, &g.state->nW, s);
+        launch_mark_neighbours(g, g.listR, &g.state->nR, g.h >= 2 ? g.listC[(g.h - 1) & 1] : nullptr,
+                               rcs + kRcC + g.h - 1, g.h, rcs + kRcW + g.h, s);
+        launch_stale_sampled(g, g.listW, rcs + kRcW + g.h, s);
     }
     prof_begin(g, kProfPeel, s);
     k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm);
-    k_advance<<<1, 1, 0, s>>>(g.state);
-    count_launch(g, 2);
+    count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     return KH_OK;
 }

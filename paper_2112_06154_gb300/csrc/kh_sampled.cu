@@ -474,19 +474,21 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
-// Alive neighbours of the listed nodes join the work list once per stamp
-// (round, phase).  One CTA per listed node.
+// Alive neighbours of the listed nodes (two lists, the second optional) join
+// the work list once per stamp (round, phase).  One CTA per listed node.
 __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
-                            const int32_t* __restrict__ list, const int* __restrict__ nlist,
+                            const int32_t* __restrict__ list1, const int* __restrict__ nlist1,
+                            const int32_t* __restrict__ list2, const int* __restrict__ nlist2,
                             int32_t* __restrict__ wl, int* nwl, const DevState* __restrict__ st,
                             int phase, int64_t cap, unsigned long long* bytes) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nin = *nlist;
+    const int n1 = *nlist1;
+    const int nin = n1 + (list2 ? *nlist2 : 0);
     const int stamp = st->round * kPhaseStride + phase;
     unsigned long long my_bytes = 0;
     for (int64_t i = blockIdx.x; i < nin; i += gridDim.x) {
-        const int w = list[i];
+        const int w = i < n1 ? list1[i] : list2[i - n1];
         const int64_t b = rowptr[w], e = rowptr[w + 1];
         if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
         for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
@@ -585,7 +587,7 @@ int table_lg(int64_t M) {
 }
 
 int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
-                 int64_t count_static, int track, cudaStream_t s) {
+                 int64_t count_static, int track, cudaStream_t s, int round_mode) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
     LevelArgs a;
@@ -610,22 +612,35 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.count_static = count_static;
     a.track = track;
     a.changed = g.listC[level & 1];
-    a.n_changed = &g.state->nC[level & 1];
     a.heavy = g.listH;
-    a.n_heavy = &g.state->nH;
-    a.work_ctr = &g.state->work_ctr[1];
     a.err = &g.state->err;
     a.updates = &g.state->updates;
+    int* rc = g.state->rc;
+    if (round_mode == 1) {
+        a.n_changed = rc + kRcC + level;
+        a.n_heavy = rc + kRcLevelHeavy + level;
+        a.work_ctr = rc + kRcLevelWork + level;
+    } else if (round_mode == 2) {
+        a.n_changed = rc + kRcC + 0;  // unused: the refine does not track changes
+        a.n_heavy = rc + kRcRefineHeavy;
+        a.work_ctr = rc + kRcRefineWork;
+    } else {
+        a.n_changed = &g.state->nC[level & 1];
+        a.n_heavy = &g.state->nH;
+        a.work_ctr = &g.state->work_ctr[1];
+    }
     cudaError_t e;
-    if (track) {
+    if (track && round_mode == 0) {
         e = cudaMemsetAsync(a.n_changed, 0, sizeof(int), s);
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_changed");
     }
     const int64_t work = worklist ? g.n : count_static;
     if (level == 1) {
         a.bytes = &g.state->bytes[kProfLevel1];
-        e = cudaMemsetAsync(a.n_heavy, 0, sizeof(int), s);
-        if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_heavy");
+        if (round_mode == 0) {
+            e = cudaMemsetAsync(a.n_heavy, 0, sizeof(int), s);
+            if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_heavy");
+        }
         int64_t grid = (work + (kL1Threads / 32) - 1) / (kL1Threads / 32);
         const int64_t gmax = (int64_t)g.ctx->sm_count * 8;
         if (grid > gmax) grid = gmax;
@@ -649,8 +664,10 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     int64_t grid = (int64_t)g.ctx->sm_count * per_sm;
     if (work < grid) grid = work;
     if (grid < 1) grid = 1;
-    e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
-    if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    if (round_mode == 0) {
+        e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+    }
     prof_begin(g, kProfLevelU, s);
     k_levelU<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
     count_launch(g, 1);
@@ -658,12 +675,12 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     return KH_OK;
 }
 
-void launch_mark_neighbours(Graph& g, const int* list, const int* d_count, int phase,
-                            cudaStream_t s) {
+void launch_mark_neighbours(Graph& g, const int* list1, const int* cnt1, const int* list2,
+                            const int* cnt2, int phase, int* out_count, cudaStream_t s) {
     const int grid = g.ctx->sm_count * 8;
     prof_begin(g, kProfFrontier, s);
-    k_mark_nbrs<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, list, d_count, g.listW,
-                                     &g.state->nW, g.state, phase, g.n,
+    k_mark_nbrs<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, list1, cnt1, list2, cnt2,
+                                     g.listW, out_count, g.state, phase, g.n,
                                      &g.state->bytes[kProfFrontier]);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
