@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
+                                    "sampled3", "exact2"],
+                   help="run one operation of the step once (a target for profilers) and exit")
     return p.parse_args()
 
 
@@ -364,9 +367,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_op(args):
+    """One operation of the step on the same workload, once, for ncu."""
+    import torch
+    from paper_2112_06154_gb300 import khcore as K
+    K.load(build_if_missing=True)
+    rp, cl = make_graph()
+    ctx = K.kh_ctx_create(0)
+    G = K.kh_graph_load_csr(ctx, rp, cl)
+    K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+    op, h = args.op[:-1], int(args.op[-1])
+    K.kh_set_h(G, h)
+    t0 = time.perf_counter()
+    fn = {"hdeg": K.kh_hdegree_exact, "counts": lambda g: K.kh_sampled_counts(g, J_LO, J_HI),
+          "est": K.kh_estimate, "sampled": K.kh_core_sampled, "exact": K.kh_core_exact}[op]
+    fn(G)
+    K.kh_sync(G)
+    print(json.dumps({"op": args.op, "seconds": time.perf_counter() - t0,
+                      "launches": K.kh_launch_count(G)}), flush=True)
+    G.close()
+    ctx.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.op:
+        run_op(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
