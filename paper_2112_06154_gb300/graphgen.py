@@ -39,14 +39,20 @@ def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray):
     u, v = u[keep], v[keep]
     lo = np.minimum(u, v)
     hi = np.maximum(u, v)
-    key = np.unique(lo * n + hi)
+    key = lo * n + hi
+    key.sort()
+    if key.size:
+        first = np.empty(key.size, dtype=bool)
+        first[0] = True
+        np.not_equal(key[1:], key[:-1], out=first[1:])
+        key = key[first]
     lo = key // n
     hi = key - lo * n
-    src = np.concatenate([lo, hi])
-    dst = np.concatenate([hi, lo])
-    order = np.lexsort((dst, src))
-    src = src[order]
-    dst = dst[order]
+    # both directions as one sorted key array: (src, dst) -> src * n + dst
+    both = np.concatenate([key, hi * n + lo])
+    both.sort()
+    src = both // n
+    dst = both - src * n
     counts = np.bincount(src, minlength=n).astype(np.int64)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
@@ -92,26 +98,33 @@ def chung_lu(n: int, avg_deg: float, gamma: float, max_deg: int, seed: int):
 
 
 def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int):
-    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale edge draws."""
+    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale edge draws.
+
+    Each draw descends `scale` levels; at each level one uniform number picks
+    quadrant a (0,0), b (0,1), c (1,0) or d (1,1), appending one bit to the
+    row and column ids (most significant first)."""
     rng = np.random.default_rng(seed)
     n = 1 << scale
     m_draw = edge_factor * n
-    u = np.zeros(m_draw, dtype=np.int64)
-    v = np.zeros(m_draw, dtype=np.int64)
-    ab = a + b
-    abc = a + b + c
+    u = np.empty(m_draw, dtype=np.int64)
+    v = np.empty(m_draw, dtype=np.int64)
+    ab = np.float32(a + b)
+    abc = np.float32(a + b + c)
+    a32 = np.float32(a)
     chunk = 1 << 24
     for s in range(0, m_draw, chunk):
         e = min(m_draw, s + chunk)
-        uu = np.zeros(e - s, dtype=np.int64)
-        vv = np.zeros(e - s, dtype=np.int64)
-        for lvl in range(scale):
-            x = rng.random(e - s)
-            bit = np.int64(1) << np.int64(scale - 1 - lvl)
-            down = x >= ab                      # quadrants c, d: row bit set
-            right = ((x >= a) & (x < ab)) | (x >= abc)  # quadrants b, d: column bit set
-            uu |= np.where(down, bit, 0)
-            vv |= np.where(right, bit, 0)
+        uu = np.zeros(e - s, dtype=np.uint32)
+        vv = np.zeros(e - s, dtype=np.uint32)
+        for _ in range(scale):
+            x = rng.random(e - s, dtype=np.float32)
+            q = (x >= a32).astype(np.uint32)
+            q += x >= ab
+            q += x >= abc          # quadrant index 0..3 = a, b, c, d
+            uu <<= 1
+            uu |= q >> 1
+            vv <<= 1
+            vv |= q & 1
         u[s:e] = uu
         v[s:e] = vv
     perm = rng.permutation(n).astype(np.int64)

@@ -276,3 +276,31 @@ def test_core_sampled_families(ctx, family, h, M):
     ro, rounds, _ = K.kh_peel_info(G)
     assert rounds == steps and (ro == wround).all()
     G.close()
+
+
+def _sparse_big():
+    """n = 1,000,000 nodes (above the 819,200-node shared-memory bitmap limit,
+    so the BFS keeps its visited set in global memory): a Chung-Lu component
+    on the first 30,000 ids, the rest isolated."""
+    rp0, cl0 = gg.chung_lu(30000, 12, 2.4, 400, 41)
+    n = 1_000_000
+    rp = np.concatenate([rp0, np.full(n - 30000, rp0[-1], dtype=np.int64)])
+    return rp, cl0
+
+
+def test_global_bitmap_bfs_and_peels(ctx):
+    rp, cl = _sparse_big()
+    for h in (2, 3):
+        G = load(ctx, (rp, cl), h=h, M=30)
+        deg = K.kh_hdegree_exact(G)
+        want = O.hdegree_exact(rp, cl, h)
+        assert (deg == want).all()
+        cnt = K.kh_sampled_counts(G, 0, 4)
+        r = O.ranks(rp.size - 1, 1)
+        assert (cnt[:30000] == O.fixed_counts(rp[:30001], cl, r[:30000], h, 0, 4)).all()
+        assert (cnt[30000:] == 0).all()
+        if h == 2:
+            core = K.kh_core_exact(G)
+            assert (core[:30000] == O.core_exact(rp[:30001], cl, 2)[0]).all()
+            assert (core[30000:] == 0).all()
+        G.close()
