@@ -70,6 +70,23 @@ int kh_graph_load_csr(kh_ctx *ctx, int64_t n, const int64_t *rowptr, const int32
                       uint32_t flags, kh_graph **out);
 int kh_graph_free(kh_graph *g);
 
+/* Load many graphs packed in one CSR as one batch (the batched form of the
+ * decomposition; the paper processes one graph at a time).  Graph q owns
+ * nodes vtx_off[q] .. vtx_off[q+1]-1 (vtx_off: int64[ngraphs+1], host memory,
+ * vtx_off[0] = 0) and its column indices are global ids inside that range;
+ * rowptr (int64[N+1]) and col follow kh_graph_load_csr (KH_DEVICE_PTR
+ * applies to them).  h_per_graph (int32[ngraphs], host, may be NULL for h = 2)
+ * sets each graph's h.  M is Eq. (buffer) of each graph's own node count
+ * (eps 0.5, delta 0.05; kh_set_sampling with M_or_0 == 0 recomputes it per
+ * graph, M_or_0 > 0 sets one M for all), and ranks use each node's id inside
+ * its graph, so every result equals the result of loading that graph alone.
+ * Results are per node of the batch (length N = vtx_off[ngraphs]).
+ * kh_set_h on a batch replaces the per-graph h by one h for every graph.
+ * KH_EGRAPH also when an edge joins two graphs. */
+int kh_graph_load_batch(kh_ctx *ctx, int32_t ngraphs, const int64_t *vtx_off, const int64_t *rowptr,
+                        const int32_t *col, const int32_t *h_per_graph, uint32_t flags,
+                        kh_graph **out);
+
 /* Number of nodes of a loaded graph. */
 int kh_graph_n(kh_graph *g, int64_t *n);
 
@@ -85,7 +102,7 @@ int kh_set_h(kh_graph *g, int32_t h);
  * delta 0.05. */
 int kh_set_sampling(kh_graph *g, uint64_t seed, int64_t M_or_0, double eps, double delta);
 
-/* The budget M in force. */
+/* The budget M in force (for a batch with per-graph M: the largest). */
 int kh_get_M(kh_graph *g, int64_t *M);
 
 /* Ranks r[v], uint8[n] (Sec. 3; Alg. 4 first loop). */

@@ -2,7 +2,9 @@
 // contexts, graph loading and validation, parameters, and the calls that run
 // the exact and sampled paths.  Every device array of a graph is allocated
 // here once and reused across calls.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -125,19 +127,19 @@ static int prof_collect(Graph& g) {
 }
 
 int ensure_lists(Graph& g) {
-    // lists for levels 1..h-1, sizes/levels for 1..h
-    const int64_t need_keys = (int64_t)(g.h - 1) * g.n * g.cap;
+    // lists for levels 1..hmax-1, sizes/levels for 1..hmax
+    const int64_t need_keys = (int64_t)(g.hmax - 1) * g.n * g.cap;
     if (g.keys && g.keys_levels * g.n * g.cap < need_keys) dfree(&g.keys);
-    if (g.lsz && g.lvl_alloc < g.h) {
+    if (g.lsz && g.lvl_alloc < g.hmax) {
         dfree(&g.lsz);
         dfree(&g.lk);
     }
     int rc;
     if (need_keys > 0) {
         if ((rc = dalloc(g.ctx, &g.keys, (size_t)need_keys, "sample lists"))) return rc;
-        g.keys_levels = g.h - 1;
+        g.keys_levels = g.hmax - 1;
     }
-    if (!g.lsz) g.lvl_alloc = g.h;
+    if (!g.lsz) g.lvl_alloc = g.hmax;
     if ((rc = dalloc(g.ctx, &g.lsz, (size_t)g.lvl_alloc * g.n, "list sizes"))) return rc;
     if ((rc = dalloc(g.ctx, &g.lk, (size_t)g.lvl_alloc * g.n, "list levels"))) return rc;
     if (!g.ranks_valid) {
@@ -157,9 +159,11 @@ int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps) {
     dfree(&g.queues);
     dfree(&g.gbitmaps);
     int rc;
-    if ((rc = dalloc(g.ctx, &g.queues, (size_t)ctas * (size_t)g.n, "BFS queues"))) return rc;
+    // a batch's BFS stays inside one graph: queues and bitmaps span its largest graph
+    const int64_t domain = g.gid ? g.max_gn : g.n;
+    if ((rc = dalloc(g.ctx, &g.queues, (size_t)ctas * (size_t)domain, "BFS queues"))) return rc;
     if (bitmaps) {
-        const size_t words = (size_t)((g.n + 31) / 32);
+        const size_t words = (size_t)((domain + 31) / 32);
         if ((rc = dalloc(g.ctx, &g.gbitmaps, (size_t)ctas * words, "BFS bitmaps"))) return rc;
     }
     g.scratch_ctas = ctas;
@@ -198,6 +202,14 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.listH);
     dfree(&g.fresh);
     dfree(&g.deadbm);
+    dfree(&g.gid);
+    dfree(&g.vtx_off);
+    dfree(&g.hv);
+    dfree(&g.Mv);
+    delete g.h_vtx_off;
+    g.h_vtx_off = nullptr;
+    delete g.h_hgraph;
+    g.h_hgraph = nullptr;
     dfree(&g.degX);
     dfree(&g.lb64);
     if (g.round_exec) cudaGraphExecDestroy(g.round_exec);
@@ -292,8 +304,11 @@ const char* kh_last_error(kh_ctx* ctx) {
     return ctx->err;
 }
 
-int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
-                      uint32_t flags, kh_graph** out) {
+namespace kh {
+// Shared by kh_graph_load_csr and kh_graph_load_batch: copy and validate the
+// CSR; host_gid (batches) makes the validation reject edges between graphs.
+static int load_graph(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
+                      uint32_t flags, const int32_t* host_gid, kh_graph** out) {
     if (!ctx || !out) return KH_EINVAL;
     *out = nullptr;
     if (n < 0 || (n > 0 && (!rowptr))) return kh::set_error(ctx, KH_EINVAL, "bad n or rowptr");
@@ -327,6 +342,7 @@ int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32
     g.n = n;
     g.nnz = nnz;
     g.h = 2;
+    g.hmin = g.hmax = 2;
     g.seed = 1;
     g.M = 0;
     g.cap = 0;
@@ -334,7 +350,8 @@ int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32
     if ((rc = kh::dalloc(ctx, &g.rowptr, (size_t)n + 1, "rowptr")) ||
         (rc = kh::dalloc(ctx, &g.col, (size_t)nnz, "col")) ||
         (rc = kh::dalloc(ctx, &g.rank, (size_t)n, "rank")) ||
-        (rc = kh::dalloc(ctx, &g.state, 1, "state"))) {
+        (rc = kh::dalloc(ctx, &g.state, 1, "state")) ||
+        (host_gid && (rc = kh::dalloc(ctx, &g.gid, (size_t)n, "graph ids")))) {
         kh::free_graph_arrays(g);
         free(G);
         return rc;
@@ -344,6 +361,8 @@ int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32
     if (ce == cudaSuccess && nnz > 0)
         ce = cudaMemcpyAsync(g.col, col, sizeof(int32_t) * (size_t)nnz, kind, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(g.state, 0, sizeof(kh::DevState), s);
+    if (ce == cudaSuccess && host_gid && n > 0)
+        ce = cudaMemcpyAsync(g.gid, host_gid, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) {
         rc = kh::check_cuda(ctx, ce, "copy CSR");
         kh::free_graph_arrays(g);
@@ -367,12 +386,80 @@ int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32
         kh::free_graph_arrays(g);
         free(G);
         return kh::set_error(ctx, KH_EGRAPH,
-                             "graph is not a simple symmetric CSR with sorted rows");
+                             host_gid ? "batch is not a simple symmetric CSR with sorted rows and "
+                                        "no edge between graphs"
+                                      : "graph is not a simple symmetric CSR with sorted rows");
     }
     rc = kh::set_M(g, kh::budget_M(n > 0 ? n : 1, 0.5, 0.05));
     if (rc) {
         kh::free_graph_arrays(g);
         free(G);
+        return rc;
+    }
+    *out = G;
+    return KH_OK;
+}
+}  // namespace kh
+
+int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
+                      uint32_t flags, kh_graph** out) {
+    return kh::load_graph(ctx, n, rowptr, col, flags, nullptr, out);
+}
+
+int kh_graph_load_batch(kh_ctx* ctx, int32_t ngraphs, const int64_t* vtx_off, const int64_t* rowptr,
+                        const int32_t* col, const int32_t* h_per_graph, uint32_t flags,
+                        kh_graph** out) {
+    if (!ctx || !out || ngraphs < 1 || !vtx_off) return KH_EINVAL;
+    *out = nullptr;
+    if (vtx_off[0] != 0) return kh::set_error(ctx, KH_EINVAL, "vtx_off[0] must be 0");
+    int64_t max_gn = 0;
+    int hmin = kh::kMaxH, hmax = 1;
+    for (int32_t q = 0; q < ngraphs; ++q) {
+        const int64_t gn = vtx_off[q + 1] - vtx_off[q];
+        if (gn < 0) return kh::set_error(ctx, KH_EINVAL, "vtx_off must be nondecreasing");
+        if (gn > max_gn) max_gn = gn;
+        const int hq = h_per_graph ? h_per_graph[q] : 2;
+        if (hq < 1 || hq > kh::kMaxH)
+            return kh::set_error(ctx, KH_EINVAL, "graph %d: h = %d outside [1, %d]", q, hq, kh::kMaxH);
+        hmin = std::min(hmin, hq);
+        hmax = std::max(hmax, hq);
+    }
+    const int64_t n = vtx_off[ngraphs];
+    if (n > (int64_t)kh::kIdMask)
+        return kh::set_error(ctx, KH_EGRAPH, "n = %lld exceeds 2^27 - 1 node ids", (long long)n);
+    std::vector<int32_t> gid((size_t)n);
+    std::vector<uint8_t> hv((size_t)n);
+    for (int32_t q = 0; q < ngraphs; ++q)
+        for (int64_t v = vtx_off[q]; v < vtx_off[q + 1]; ++v) {
+            gid[(size_t)v] = q;
+            hv[(size_t)v] = (uint8_t)(h_per_graph ? h_per_graph[q] : 2);
+        }
+    kh_graph* G = nullptr;
+    int rc = kh::load_graph(ctx, n, rowptr, col, flags, gid.data(), &G);
+    if (rc) return rc;
+    Graph& g = G->g;
+    g.ngraphs = ngraphs;
+    g.max_gn = max_gn;
+    g.h = hmax;
+    g.hmin = hmin;
+    g.hmax = hmax;
+    g.h_vtx_off = new std::vector<int64_t>(vtx_off, vtx_off + ngraphs + 1);
+    if ((rc = kh::dalloc(ctx, &g.vtx_off, (size_t)ngraphs + 1, "vtx_off")) ||
+        (rc = kh::dalloc(ctx, &g.hv, (size_t)n, "per-node h"))) {
+        kh_graph_free(G);
+        return rc;
+    }
+    cudaError_t ce = cudaMemcpy(g.vtx_off, vtx_off, sizeof(int64_t) * (size_t)(ngraphs + 1),
+                                cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && n > 0) ce = cudaMemcpy(g.hv, hv.data(), (size_t)n, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        rc = kh::check_cuda(ctx, ce, "copy batch tables");
+        kh_graph_free(G);
+        return rc;
+    }
+    rc = kh_set_sampling(G, 1, 0, 0.5, 0.05);  // per-graph M from each graph's n
+    if (rc) {
+        kh_graph_free(G);
         return rc;
     }
     *out = G;
@@ -397,7 +484,13 @@ int kh_graph_n(kh_graph* G, int64_t* n) {
 int kh_set_h(kh_graph* G, int32_t h) {
     if (!G) return KH_EINVAL;
     if (h < 1 || h > kh::kMaxH) return kh::set_error(G->g.ctx, KH_EINVAL, "h = %d outside [1, %d]", h, kh::kMaxH);
-    G->g.h = h;
+    Graph& g = G->g;
+    cudaSetDevice(g.ctx->device);
+    if (g.hv) {  // a batch: one h for every graph from now on
+        cudaStreamSynchronize(g.ctx->stream);
+        kh::dfree(&g.hv);
+    }
+    g.h = g.hmin = g.hmax = h;
     return KH_OK;
 }
 
@@ -410,6 +503,32 @@ int kh_set_sampling(kh_graph* G, uint64_t seed, int64_t M_or_0, double eps, doub
         if (!(eps > 0.0) || !(delta > 0.0) || !(delta < 1.0) || !std::isfinite(eps))
             return kh::set_error(g.ctx, KH_EINVAL, "need eps > 0 and 0 < delta < 1");
         M = kh::budget_M(g.n > 0 ? g.n : 1, eps, delta);
+    }
+    cudaSetDevice(g.ctx->device);
+    if (g.h_vtx_off) {
+        // a batch: M of Eq. (buffer) from each graph's own n, or one M for all
+        cudaStreamSynchronize(g.ctx->stream);
+        kh::dfree(&g.Mv);
+        if (M_or_0 == 0) {
+            const std::vector<int64_t>& off = *g.h_vtx_off;
+            std::vector<int32_t> mv((size_t)g.n);
+            int64_t mmax = 1;
+            for (size_t q = 0; q + 1 < off.size(); ++q) {
+                const int64_t gn = off[q + 1] - off[q];
+                const int64_t Mg = kh::budget_M(gn > 0 ? gn : 1, eps, delta);
+                if (Mg < 1 || Mg > kh::kMaxM)
+                    return kh::set_error(g.ctx, KH_EINVAL, "graph %zu: M = %lld outside [1, %d]", q,
+                                         (long long)Mg, kh::kMaxM);
+                if (Mg > mmax) mmax = Mg;
+                for (int64_t v = off[q]; v < off[q + 1]; ++v) mv[(size_t)v] = (int32_t)Mg;
+            }
+            int rc0 = kh::dalloc(g.ctx, &g.Mv, (size_t)g.n, "per-node M");
+            if (rc0) return rc0;
+            if (g.n > 0)
+                KH_CUDA_TRY(g.ctx, cudaMemcpy(g.Mv, mv.data(), sizeof(int32_t) * (size_t)g.n,
+                                              cudaMemcpyHostToDevice));
+            M = mmax;  // sizes the list slots and hash tables
+        }
     }
     int rc = kh::set_M(g, M);
     if (rc) return rc;
@@ -493,10 +612,14 @@ int kh_estimate(kh_graph* G, uint64_t* est, uint8_t* level, int32_t* bsize, uint
     cudaSetDevice(g.ctx->device);
     int rc = kh::run_estimate_all(g);
     if (rc) return rc;
-    const size_t off = (size_t)(g.h - 1) * (size_t)g.n;
+    // each node's last level (h of its graph) into scratch, then out
+    uint8_t* lvl_tmp = reinterpret_cast<uint8_t*>(g.listB);
+    int32_t* bs_tmp = g.listA;
+    kh::launch_gather_last(g, lvl_tmp, bs_tmp, g.ctx->stream);
+    KH_CUDA_TRY(g.ctx, cudaGetLastError());
     rc = kh::copy_out(g, est, g.d64, sizeof(uint64_t) * (size_t)g.n, flags);
-    if (!rc && level) rc = kh::copy_out(g, level, g.lk + off, (size_t)g.n, flags);
-    if (!rc && bsize) rc = kh::copy_out(g, bsize, g.lsz + off, sizeof(int32_t) * (size_t)g.n, flags);
+    if (!rc && level) rc = kh::copy_out(g, level, lvl_tmp, (size_t)g.n, flags);
+    if (!rc && bsize) rc = kh::copy_out(g, bsize, bs_tmp, sizeof(int32_t) * (size_t)g.n, flags);
     return rc;
 }
 

@@ -32,10 +32,14 @@ __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_ranks(uint8_t* __restrict__ r, int64_t n, uint64_t seed) {
+// In a batch of graphs a node's counter is its id inside its own graph, so
+// each graph gets the ranks it would get alone.
+__global__ void k_ranks(uint8_t* __restrict__ r, int64_t n, uint64_t seed,
+                        const int32_t* __restrict__ gid, const int64_t* __restrict__ vtx_off) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
-        const uint64_t x = splitmix_mix(seed + (uint64_t)(u + 1) * 0x9E3779B97F4A7C15ull);
+        const int64_t local = gid ? u - vtx_off[gid[u]] : u;
+        const uint64_t x = splitmix_mix(seed + (uint64_t)(local + 1) * 0x9E3779B97F4A7C15ull);
         // trailing zeros, capped at 31: geometric(1/2) rank of Sec. 3
         r[u] = (uint8_t)(__ffsll((long long)(x | (1ull << 31))) - 1);
     }
@@ -44,7 +48,7 @@ __global__ void k_ranks(uint8_t* __restrict__ r, int64_t n, uint64_t seed) {
 // One warp per row: rows strictly increasing, ids in range, no self-loops,
 // and every edge (u, v) has its reverse (binary search in row v).
 __global__ void k_validate(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                           int64_t n, int64_t nnz, int* err) {
+                           int64_t n, int64_t nnz, int* err, const int32_t* __restrict__ gid) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
@@ -56,6 +60,7 @@ __global__ void k_validate(const int64_t* __restrict__ rowptr, const int32_t* __
         for (int64_t k = b + lane; k < e; k += 32) {
             const int32_t v = col[k];
             bool bad = v < 0 || (int64_t)v >= n || v == (int32_t)u;
+            if (!bad && gid && gid[v] != gid[u]) bad = true;  // batch: no edge between graphs
             if (!bad && k > b && col[k - 1] >= v) bad = true;
             int64_t lo = 0, hi = -1;
             if (!bad) {
@@ -101,6 +106,11 @@ struct BfsArgs {
     unsigned long long* bytes;  // algorithmic bytes: 8 + 4 deg per expanded vertex, 4 per result
     const int* skip;            // nonzero: the exact early stop fired, nothing to do
     const uint32_t* deadbm;     // removed-node bitmap (shared-memory mode): seeds the visited set
+    // batches: graph of each node, first node of each graph, per-node h; the
+    // visited bitmap is indexed by the id inside the source's graph
+    const int32_t* gid;
+    const int64_t* vtx_off;
+    const uint8_t* hv;
 };
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
@@ -108,13 +118,14 @@ struct BfsArgs {
 template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
 __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
                                       int* s_hist, bool valid, int32_t u, bool push, int lane,
-                                      int& my) {
+                                      int& my, int32_t base) {
     bool isnew = false;
     // seeded: removed nodes already have their bit set, no alive lookup needed;
     // ALLALIVE: the whole graph, no alive array at all
     if (valid && (SEEDED || ALLALIVE || a.alive[u] == 1)) {
-        const uint32_t bit = 1u << (u & 31);
-        uint32_t* wp = bm + (u >> 5);
+        const int32_t lu = u - base;
+        const uint32_t bit = 1u << (lu & 31);
+        uint32_t* wp = bm + (lu >> 5);
         if (!(*(volatile uint32_t*)wp & bit)) {
             const uint32_t old = atomicOr(wp, bit);
             isnew = !(old & bit);
@@ -145,7 +156,8 @@ __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q
 template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
 __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
                                            int* s_hist, int64_t b, int64_t e, int64_t first,
-                                           int64_t stride, bool push, int lane, int& my) {
+                                           int64_t stride, bool push, int lane, int& my,
+                                           int32_t base) {
     for (int64_t k0 = b + first; k0 < e; k0 += stride) {
         int32_t u[4];
         bool val[4];
@@ -157,7 +169,8 @@ __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32
         }
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq)
-            visit<RANKS, SEEDED, ALLALIVE>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, lane, my);
+            visit<RANKS, SEEDED, ALLALIVE>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, lane, my,
+                                           base);
     }
 }
 
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     if (total == 0) return;
     unsigned long long my_bytes = 0;
 
-    const bool seeded = SMEM && a.deadbm != nullptr;
+    const bool seeded = SMEM && a.deadbm != nullptr && a.gid == nullptr;
     if (!seeded) {
         for (int i = tid; i < a.words; i += blockDim.x) bm[i] = 0u;
         __syncthreads();
@@ -201,19 +214,21 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             for (int i = (w4 << 2) + tid; i < a.words; i += blockDim.x) bm[i] = __ldg(a.deadbm + i);
             __syncthreads();
         }
+        const int32_t base = a.gid ? (int32_t)a.vtx_off[a.gid[v]] : 0;
+        const int hsrc = a.hv ? (int)a.hv[v] : a.h;
         if (tid == 0) {
             q[0] = v;
             s_qtail = 1;
             s_count = 0;
-            bm[v >> 5] |= 1u << (v & 31);
+            bm[(v - base) >> 5] |= 1u << ((v - base) & 31);
         }
         if (RANKS && tid < 32) s_hist[tid] = 0;
         __syncthreads();
         int fs = 0, fe = 1, my = 0;
-        for (int d = 0; d < a.h; ++d) {
+        for (int d = 0; d < hsrc; ++d) {
             // vertices found at distance d+1 are queued if they will be expanded,
             // or, in global-bitmap mode, so the bitmap can be cleared by a walk
-            const bool push = (d + 1 < a.h) || !SMEM;
+            const bool push = (d + 1 < hsrc) || !SMEM;
             if (tid == 0) s_nheavy = 0;
             __syncthreads();
             const bool single = (fe - fs) == 1;
@@ -231,10 +246,11 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                     }
                 }
                 if (seeded)
-                    expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my);
+                    expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my,
+                                            base);
                 else
                     expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push,
-                                                       lane, my);
+                                                       lane, my, base);
             }
             __syncthreads();
             const int nh = min(s_nheavy, kMaxHeavy);
@@ -243,10 +259,10 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
                 if (seeded)
                     expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
-                                            4 * blockDim.x, push, lane, my);
+                                            4 * blockDim.x, push, lane, my, base);
                 else
                     expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
-                                                       4 * blockDim.x, push, lane, my);
+                                                       4 * blockDim.x, push, lane, my, base);
             }
             __syncthreads();
             fs = fe;
@@ -276,7 +292,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             for (int i = (w4 << 2) + tid; i < a.words; i += blockDim.x) bm[i] = 0u;
         } else {
             const int qt = min(s_qtail, (int)a.qcap);
-            for (int i = tid; i < qt; i += blockDim.x) bm[q[i] >> 5] = 0u;
+            for (int i = tid; i < qt; i += blockDim.x) bm[(q[i] - base) >> 5] = 0u;
         }
         __syncthreads();
     }
@@ -293,7 +309,8 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
                            const int32_t* __restrict__ fin, const int* __restrict__ nfin,
                            int32_t* __restrict__ fout, int* nfout, int32_t* __restrict__ wl, int* nwl,
                            const DevState* __restrict__ st, int push_next, int64_t cap,
-                           unsigned long long* bytes, int32_t* __restrict__ degX) {
+                           unsigned long long* bytes, int32_t* __restrict__ degX,
+                           const uint8_t* __restrict__ hv, int hop) {
     if (st->early) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nin = *nfin;
@@ -316,7 +333,8 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
                 if (au != 0 && *(volatile int32_t*)(seen + u) != stamp)
                     isnew = atomicExch(seen + u, stamp) != stamp;
             }
-            const bool to_f = isnew && push_next;
+            // batches: a node is expanded further only while hop < its graph's h
+            const bool to_f = isnew && (hv ? hop < (int)hv[u] : push_next != 0);
             const bool to_w = isnew && au == 1;
             uint32_t m1 = __ballot_sync(kFull, to_f);
             uint32_t m2 = __ballot_sync(kFull, to_w);
@@ -350,7 +368,7 @@ __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t*
                               const int32_t* __restrict__ list, const int* __restrict__ nlist,
                               int64_t n, uint8_t* __restrict__ fresh,
                               unsigned long long* __restrict__ lb, const DevState* __restrict__ st,
-                              unsigned long long* bytes, int h) {
+                              unsigned long long* bytes, int h_all, const uint8_t* __restrict__ hv) {
     if (st->early) return;
     __shared__ int s_max[kBfsThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -359,6 +377,7 @@ __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t*
     for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
         const int v = list ? list[i] : (int)i;
         if (alive[v] != 1) continue;  // block-uniform
+        const int h = hv ? (int)hv[v] : h_all;
         const int64_t b = rowptr[v], e = rowptr[v + 1];
         int m = 0;
         if (h >= 2) {
@@ -393,14 +412,14 @@ int pick_grid(int sm, int per_sm, int64_t work) {
 void launch_ranks(const Graph& g, cudaStream_t s) {
     if (g.n == 0) return;
     const int grid = pick_grid(g.ctx->sm_count, 4, (g.n + 255) / 256);
-    k_ranks<<<grid, 256, 0, s>>>(g.rank, g.n, g.seed);
+    k_ranks<<<grid, 256, 0, s>>>(g.rank, g.n, g.seed, g.gid, g.vtx_off);
     count_launch(const_cast<Graph&>(g), 1);
 }
 
 void launch_validate(const Graph& g, int* d_err, cudaStream_t s) {
     if (g.n == 0) return;
     const int grid = pick_grid(g.ctx->sm_count, 8, (g.n * 32 + 255) / 256);
-    k_validate<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.n, g.nnz, d_err);
+    k_validate<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.n, g.nnz, d_err, g.gid);
     count_launch(const_cast<Graph&>(g), 1);
 }
 
@@ -408,7 +427,9 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
                 int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s, int* round_ctr) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
-    const int words = (int)((g.n + 31) / 32);
+    // batches index the visited bitmap inside the source's graph
+    const int64_t domain = g.gid ? g.max_gn : g.n;
+    const int words = (int)((domain + 31) / 32);
     const int64_t words_padded = ((int64_t)words + 3) & ~(int64_t)3;
     const bool smem = words_padded * 4 <= kSmemBitmapMax;
     const size_t dyn = smem ? (size_t)words_padded * 4 : 0;
@@ -444,7 +465,7 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.jlo = jlo;
     a.nj = nj;
     a.queues = g.queues;
-    a.qcap = g.n;
+    a.qcap = domain;  // matches the per-CTA queue allocation of ensure_bfs_scratch
     a.gbitmaps = g.gbitmaps;
     a.work_ctr = round_ctr ? round_ctr : &g.state->work_ctr[0];
     a.err = &g.state->err;
@@ -452,6 +473,9 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.bytes = &g.state->bytes[kProfBfs];
     a.skip = worklist ? &g.state->early : nullptr;
     a.deadbm = g.deadbm;
+    a.gid = g.gid;
+    a.vtx_off = g.vtx_off;
+    a.hv = g.hv;
     if (!round_ctr) {
         e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
@@ -473,7 +497,8 @@ void launch_ball_hop(Graph& g, int hop, cudaStream_t s) {
     prof_begin(g, kProfFrontier, s);
     k_ball_hop<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, fin, nfin, fout, nfout,
                                     g.listW, &g.state->rc[kRcW], g.state, hop < g.h ? 1 : 0, g.n,
-                                    &g.state->bytes[kProfFrontier], hop == 1 ? g.degX : nullptr);
+                                    &g.state->bytes[kProfFrontier], hop == 1 ? g.degX : nullptr,
+                                    g.hv, hop);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }
@@ -484,7 +509,7 @@ void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStrea
     prof_begin(g, kProfFrontier, s);
     k_stale_exact<<<grid, kBfsThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.degX, list, d_count, g.n,
                                        g.fresh, g.lb64, g.state, &g.state->bytes[kProfFrontier],
-                                       g.h);
+                                       g.h, g.hv);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

@@ -106,14 +106,18 @@ void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStrea
 // level `level` inside a round; 2: refine of the last level inside a round
 // (per-round counters, no memsets).
 int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
-                 int64_t count_static, int track, cudaStream_t s, int round_mode = 0);
+                 int64_t count_static, int track, cudaStream_t s, int round_mode = 0,
+                 int skip_last = -1);
 // alive neighbours of the nodes in list1 and list2 (may be nullptr) join the
 // work list listW (count *out_count), deduplicated by stamp phase
 void launch_mark_neighbours(Graph& g, const int* list1, const int* cnt1, const int* list2,
                             const int* cnt2, int phase, int* out_count, cudaStream_t s);
 // sampled mode: mark the nodes of `list` (nullptr: all) stale at the last
 // level with a lower bound of their estimate
-void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s);
+void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s,
+                          int only_h = 0);
+// each node's last-level k and |B| into device arrays (either may be nullptr)
+void launch_gather_last(Graph& g, uint8_t* lvl_out, int32_t* bs_out, cudaStream_t s);
 
 // ---- launchers (kh_peel.cu) --------------------------------------------------
 int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, bool out_dev);
@@ -166,6 +170,16 @@ struct Graph {
     uint32_t *gbitmaps;
     int64_t scratch_ctas;
     int32_t *listH;         // heavy nodes deferred by the level-1 warp kernel
+    // batches of graphs packed in one CSR (all nullptr for a single graph)
+    int32_t *gid;           // graph of each node
+    int64_t *vtx_off;       // first node of each graph, ngraphs + 1 entries
+    uint8_t *hv;            // per-node h (nullptr: g.h for every node)
+    int32_t *Mv;            // per-node M (nullptr: g.M for every node)
+    int64_t ngraphs;
+    int64_t max_gn;         // largest graph of the batch
+    int hmin, hmax;         // range of h over the nodes
+    std::vector<int64_t>* h_vtx_off;  // host copy of vtx_off (per-graph M)
+    std::vector<int32_t>* h_hgraph;   // host copy of the per-graph h
     // lazy refinement of the last level: fresh[v] = d[v] is exact for the
     // current alive set; otherwise d[v] is an upper bound (d never grows as
     // nodes leave) and lb64[v] (exact mode) a lower bound
@@ -186,7 +200,7 @@ struct Graph {
     int64_t prof_launches[kProfKinds];
     // cached CUDA graph of a batch of peeling rounds
     cudaGraphExec_t round_exec;
-    int round_exec_key[6];
+    int round_exec_key[8];
     int64_t round_exec_kernels;  // kernels in one replay of round_exec
     // kernels launched on behalf of this graph (graph replays count their nodes)
     int64_t launches;

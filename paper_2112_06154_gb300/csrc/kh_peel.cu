@@ -257,7 +257,9 @@ int start_peel(Graph& g, bool sampled, cudaStream_t s) {
     const int grid = peel_grid(g);
     int rc = KH_OK;
     if (sampled) {
-        for (int i = 1; i < g.h && rc == KH_OK; ++i) rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s);
+        // every list below each node's last level; the last level itself stays lazy
+        for (int i = 1; i < g.hmax && rc == KH_OK; ++i)
+            rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s, 0, 1);
         if (rc) return rc;
         KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.d64, 0xff, sizeof(unsigned long long) * (size_t)g.n, s));
         launch_stale_sampled(g, nullptr, nullptr, s);
@@ -316,21 +318,20 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     if (!sampled) {
         // the ball of R in the old graph: alive degrees drop (hop 1), the
         // nodes within h hops become stale with new lower bounds
-        for (int hop = 1; hop <= g.h; ++hop) launch_ball_hop(g, hop, s);
+        for (int hop = 1; hop <= g.hmax; ++hop) launch_ball_hop(g, hop, s);
         launch_stale_exact(g, g.listW, &g.state->rc[kRcW], s);
     } else {
         int* rcs = g.state->rc;
-        for (int i = 1; i < g.h && rc == KH_OK; ++i) {
-            // level i: A(R), plus A(nodes changed at level i-1)
+        for (int i = 1; i <= g.hmax && rc == KH_OK; ++i) {
+            // level i candidates: A(R), plus A(nodes whose level i-1 changed)
             launch_mark_neighbours(g, g.listR, &g.state->nR, i >= 2 ? g.listC[(i - 1) & 1] : nullptr,
                                    rcs + kRcC + i - 1, i, rcs + kRcW + i, s);
-            rc = launch_level(g, i, g.listW, rcs + kRcW + i, 0, 1, s, 1);
+            // nodes with more levels recompute level i (tracking changes) ...
+            if (i < g.hmax) rc = launch_level(g, i, g.listW, rcs + kRcW + i, 0, 1, s, 1);
+            // ... nodes whose last level is i become stale (lazy refine)
+            if (i >= g.hmin) launch_stale_sampled(g, g.listW, rcs + kRcW + i, s, i);
         }
         if (rc) return rc;
-        // the last level of A(R) and of A(changed at h-1) becomes stale
-        launch_mark_neighbours(g, g.listR, &g.state->nR, g.h >= 2 ? g.listC[(g.h - 1) & 1] : nullptr,
-                               rcs + kRcC + g.h - 1, g.h, rcs + kRcW + g.h, s);
-        launch_stale_sampled(g, g.listW, rcs + kRcW + g.h, s);
     }
     prof_begin(g, kProfPeel, s);
     k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm);
@@ -347,7 +348,10 @@ int check_state_err(Graph& g, const DevState& hs) {
 
 // Capture kRoundsPerGraph rounds into an executable graph (cached per shape).
 int round_graph(Graph& g, bool sampled, cudaStream_t s, cudaGraphExec_t* out) {
-    const int key[6] = {sampled ? 1 : 0, g.h, (int)g.M, (int)g.cap, (int)g.scratch_ctas, 1};
+    // everything a captured launch bakes in: mode, h, M, slot size, scratch, batch tables
+    const int key[8] = {sampled ? 1 : 0, g.h, (int)g.M, (int)g.cap, (int)g.scratch_ctas,
+                        (int)(reinterpret_cast<uintptr_t>(g.hv) >> 4),
+                        (int)(reinterpret_cast<uintptr_t>(g.Mv) >> 4), g.hmin};
     if (g.round_exec && memcmp(key, g.round_exec_key, sizeof(key)) == 0) {
         *out = g.round_exec;
         return KH_OK;
@@ -390,7 +394,8 @@ int run_estimate_all(Graph& g) {
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->err, 0, sizeof(int), s));
-    for (int i = 1; i <= g.h && rc == KH_OK; ++i) rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s);
+    for (int i = 1; i <= g.hmax && rc == KH_OK; ++i)
+        rc = launch_level(g, i, nullptr, nullptr, g.n, 0, s, 0, 0);
     if (rc) return rc;
     int err = 0;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&err, &g.state->err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -41,17 +41,17 @@ struct LevelArgs {
     const uint8_t* alive;
     const uint8_t* rank;
     int64_t n;
-    int level;
-    int last;                  // level == h
-    int64_t M;
+    int level;                 // level to compute; 0: each node's last level h(v)
+    int h;                     // h of every node when hv is nullptr
+    const uint8_t* hv;         // per-node h (batches)
+    int skip_last;             // leave a node's last level to the lazy refine
+    int64_t M;                 // M of every node when Mv is nullptr
+    const int32_t* Mv;         // per-node M (batches)
     int64_t cap;
-    const uint32_t* keys_in;   // lists of level-1 (levels >= 2)
-    uint32_t* keys_out;        // lists of this level (when !last)
-    const int32_t* lsz_in;
-    const uint8_t* lk_in;
-    int32_t* lsz_out;
-    uint8_t* lk_out;
-    unsigned long long* est;   // estimate (when last)
+    uint32_t* keys;            // level i lists at keys + (i-1) n cap
+    int32_t* lsz;              // |B[v,i]| at lsz + (i-1) n
+    uint8_t* lk;               // k[v,i] at lk + (i-1) n
+    unsigned long long* est;   // estimate (at a node's last level)
     const int32_t* worklist;
     const int* d_count;
     int64_t count_static;
@@ -68,6 +68,40 @@ struct LevelArgs {
 
 constexpr int kL1Heavy = 512;
 
+// What one node computes in this launch: its level, whether that is its last
+// level h(v) (estimate) or an intermediate one (list), its M, and where its
+// inputs (level - 1) and outputs live.
+struct NodeLevel {
+    int lvl;
+    bool last;
+    bool skip;
+    int64_t M;
+    const uint32_t* keys_in;
+    uint32_t* keys_out;
+    const int32_t* lsz_in;
+    const uint8_t* lk_in;
+    int32_t* lsz_out;
+    uint8_t* lk_out;
+};
+
+__device__ __forceinline__ NodeLevel node_level(const LevelArgs& a, int v) {
+    NodeLevel nl;
+    const int hvv = a.hv ? (int)a.hv[v] : a.h;
+    nl.lvl = a.level ? a.level : hvv;
+    nl.last = nl.lvl == hvv;
+    nl.skip = nl.lvl > hvv || (nl.last && a.skip_last);
+    nl.M = a.Mv ? (int64_t)a.Mv[v] : a.M;
+    const size_t nn = (size_t)a.n, lc = nn * (size_t)a.cap;
+    const int L = nl.lvl;
+    nl.keys_in = L >= 2 ? a.keys + (size_t)(L - 2) * lc : nullptr;
+    nl.keys_out = (!nl.last && a.keys) ? a.keys + (size_t)(L - 1) * lc : nullptr;
+    nl.lsz_in = L >= 2 ? a.lsz + (size_t)(L - 2) * nn : nullptr;
+    nl.lk_in = L >= 2 ? a.lk + (size_t)(L - 2) * nn : nullptr;
+    nl.lsz_out = a.lsz + (size_t)(L - 1) * nn;
+    nl.lk_out = a.lk + (size_t)(L - 1) * nn;
+    return nl;
+}
+
 __device__ __forceinline__ unsigned long long estimate_of(int S, int kappa, int rv, int64_t M) {
     // Alg. 1: d = |B[v,h] \ {v}| 2^k; if k > 0, d = max(d, M 2^(k-1))
     const int T = S - (rv >= kappa ? 1 : 0);
@@ -79,11 +113,12 @@ __device__ __forceinline__ unsigned long long estimate_of(int S, int kappa, int 
     return d;
 }
 
-__device__ __forceinline__ void record_change(const LevelArgs& a, int v, int S, int kappa) {
-    const int old_s = a.lsz_out[v];
-    const int old_k = a.lk_out[v];
-    a.lsz_out[v] = S;
-    a.lk_out[v] = (uint8_t)kappa;
+__device__ __forceinline__ void record_change(const LevelArgs& a, const NodeLevel& nl, int v, int S,
+                                              int kappa) {
+    const int old_s = nl.lsz_out[v];
+    const int old_k = nl.lk_out[v];
+    nl.lsz_out[v] = S;
+    nl.lk_out[v] = (uint8_t)kappa;
     if (a.track && (old_s != S || old_k != kappa)) {
         const int p = atomicAdd(a.n_changed, 1);
         if (p < a.n) a.changed[p] = v;
@@ -106,6 +141,8 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
     for (int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < total; idx += nw) {
         const int v = a.worklist ? a.worklist[idx] : (int)idx;
         if (a.alive[v] != 1) continue;
+        const NodeLevel nl = node_level(a, v);
+        if (nl.skip || nl.lvl != 1) continue;
         const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
         if (e - b > kL1Heavy) {
             if (lane == 0) {
@@ -132,15 +169,15 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
             const int t = __shfl_down_sync(kFull, S, off);
             if (lane + off < 32) S += t;
         }
-        const uint32_t over = __ballot_sync(kFull, S > a.M);
+        const uint32_t over = __ballot_sync(kFull, S > nl.M);
         const int kappa = over ? 32 - __clz(over) : 0;
         const int Sk = __shfl_sync(kFull, S, kappa & 31);
         const int Skap = kappa < 32 ? Sk : 0;
-        if (lane == 0) my_bytes += level1_bytes(e - b, Skap, a.last);
-        if (a.last) {
+        if (lane == 0) my_bytes += level1_bytes(e - b, Skap, nl.last);
+        if (nl.last) {
             if (lane == 0) {
-                a.est[v] = estimate_of(Skap, kappa, rv, a.M);
-                record_change(a, v, Skap, kappa);
+                a.est[v] = estimate_of(Skap, kappa, rv, nl.M);
+                record_change(a, nl, v, Skap, kappa);
                 atomicAdd(a.updates, 1ull);
             }
             continue;
@@ -150,7 +187,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
         __syncwarp();
         hist[lane] = lane < 31 ? above : 0;
         __syncwarp();
-        uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
+        uint32_t* out = nl.keys_out + (size_t)v * (size_t)a.cap;
         for (int64_t k0 = b; k0 < e; k0 += 32) {
             const int64_t k = k0 + lane;
             if (k < e) {
@@ -171,7 +208,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
                 if (p < a.cap) out[p] = ((uint32_t)rv << kIdBits) | (uint32_t)v;
                 else atomicOr(a.err, kErrList);
             }
-            record_change(a, v, Skap, kappa);
+            record_change(a, nl, v, Skap, kappa);
         }
         __syncwarp();
     }
@@ -187,6 +224,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
     const int nh = *a.n_heavy;
     for (int idx = blockIdx.x; idx < nh; idx += gridDim.x) {
         const int v = a.heavy[idx];
+        const NodeLevel nl = node_level(a, v);  // deferred by k_level1: level 1, not skipped
         if (tid < 32) s_hist[tid] = 0;
         __syncthreads();
         const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
@@ -203,7 +241,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
                 const int t = __shfl_down_sync(kFull, S, off);
                 if (lane + off < 32) S += t;
             }
-            const uint32_t over = __ballot_sync(kFull, S > a.M);
+            const uint32_t over = __ballot_sync(kFull, S > nl.M);
             const int kappa = over ? 32 - __clz(over) : 0;
             const int Sk = __shfl_sync(kFull, S, kappa & 31);
             const int above = __shfl_down_sync(kFull, S, 1);
@@ -215,15 +253,15 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
         }
         __syncthreads();
         const int kappa = s_kappa, Skap = s_S;
-        if (a.last) {
+        if (nl.last) {
             if (tid == 0) {
-                a.est[v] = estimate_of(Skap, kappa, rv, a.M);
-                record_change(a, v, Skap, kappa);
+                a.est[v] = estimate_of(Skap, kappa, rv, nl.M);
+                record_change(a, nl, v, Skap, kappa);
                 atomicAdd(a.updates, 1ull);
                 atomicAdd(a.bytes, level1_bytes(e - b, Skap, 1));
             }
         } else {
-            uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
+            uint32_t* out = nl.keys_out + (size_t)v * (size_t)a.cap;
             for (int64_t k = b + tid; k < e; k += blockDim.x) {
                 const int32_t u = a.col[k];
                 if (a.alive[u] == 1) {
@@ -241,7 +279,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
                     if (p < a.cap) out[p] = ((uint32_t)rv << kIdBits) | (uint32_t)v;
                     else atomicOr(a.err, kErrList);
                 }
-                record_change(a, v, Skap, kappa);
+                record_change(a, nl, v, Skap, kappa);
                 atomicAdd(a.bytes, level1_bytes(e - b, Skap, 0));
             }
         }
@@ -294,7 +332,8 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         const int64_t idx = s_src;
         if (idx >= total) break;
         const int v = a.worklist ? a.worklist[idx] : (int)idx;
-        if (a.alive[v] != 1) {
+        const NodeLevel nl = node_level(a, v);
+        if (a.alive[v] != 1 || nl.skip || nl.lvl < 2) {
             __syncthreads();
             continue;
         }
@@ -310,7 +349,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         int myk = 0;
         for (int64_t k = b + tid; k < e; k += blockDim.x) {
             const int32_t w = a.col[k];
-            if (a.alive[w] == 1) myk = max(myk, (int)a.lk_in[w]);
+            if (a.alive[w] == 1) myk = max(myk, (int)nl.lk_in[w]);
         }
         for (int off = 16; off > 0; off >>= 1) myk = max(myk, __shfl_down_sync(kFull, myk, off));
         if (lane == 0 && myk) atomicMax(&s_t, myk);
@@ -343,7 +382,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             while (li < deg) {
                 w = a.col[b + li];
                 if (a.alive[w] == 1) {
-                    sz = min(a.lsz_in[w], (int)a.cap);
+                    sz = min(nl.lsz_in[w], (int)a.cap);
                     if (sz > pos) break;
                 }
                 li += ngroups;
@@ -354,7 +393,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 const int p = pos + gl * kKeysPerLane;
                 if (p < sz) {
                     const uint4 k4 =
-                        *reinterpret_cast<const uint4*>(a.keys_in + (size_t)w * (size_t)a.cap + p);
+                        *reinterpret_cast<const uint4*>(nl.keys_in + (size_t)w * (size_t)a.cap + p);
                     const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
                     for (int q = 0; q < kKeysPerLane; ++q) {
@@ -395,7 +434,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                     const int x = __shfl_down_sync(kFull, S, off);
                     if (lane + off < 32) S += x;
                 }
-                const uint32_t over = __ballot_sync(kFull, S > a.M);
+                const uint32_t over = __ballot_sync(kFull, S > nl.M);
                 const int pmax = over ? 31 - __clz(over) : -1;
                 if (lane == 0) {
                     const int told = s_t;
@@ -435,10 +474,10 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         for (int j = kappa; j < 32; ++j) S += s_hist[j];
         __syncthreads();
         if (tid == 0) my_bytes += 8ull + 10ull * (unsigned long long)deg + 5ull;
-        if (a.last) {
+        if (nl.last) {
             if (tid == 0) {
-                a.est[v] = estimate_of(S, kappa, rv, a.M);
-                record_change(a, v, S, kappa);
+                a.est[v] = estimate_of(S, kappa, rv, nl.M);
+                record_change(a, nl, v, S, kappa);
                 atomicAdd(a.updates, 1ull);
                 my_bytes += 8;
             }
@@ -451,7 +490,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 s_hist[tid] = above;  // start offset of rank tid
             }
             __syncthreads();
-            uint32_t* out = a.keys_out + (size_t)v * (size_t)a.cap;
+            uint32_t* out = nl.keys_out + (size_t)v * (size_t)a.cap;
             for (int i = tid; i < nu; i += blockDim.x) {
                 const int slot = used[i];
                 const uint32_t key = tab[slot];
@@ -464,7 +503,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
             }
             if (tid == 0) {
-                record_change(a, v, S, kappa);
+                record_change(a, nl, v, S, kappa);
                 my_bytes += 4ull * (unsigned long long)S;
             }
         }
@@ -530,10 +569,14 @@ __device__ __forceinline__ unsigned long long est_first(int S, int kappa, int r_
 // contains v) are inside N(v; h); Alg. 1 on either with v's rank first is at
 // most the estimate of N(v; h) (Prop. 4.2).  Only the level-(h-1) sizes and
 // levels are read.  One CTA per node.
+// Batches: a node's h and M come from its graph, and only nodes whose last
+// level is `only_h` (when nonzero) are marked.
 __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const uint8_t* __restrict__ alive, const uint8_t* __restrict__ rank,
-                                const int32_t* __restrict__ lsz_prev, const uint8_t* __restrict__ lk_prev,
-                                int64_t M, const int32_t* __restrict__ list, const int* __restrict__ nlist,
+                                const int32_t* __restrict__ lsz, const uint8_t* __restrict__ lk,
+                                int h_all, const uint8_t* __restrict__ hv, int64_t M_all,
+                                const int32_t* __restrict__ Mv, int only_h,
+                                const int32_t* __restrict__ list, const int* __restrict__ nlist,
                                 int64_t n, uint8_t* __restrict__ fresh,
                                 unsigned long long* __restrict__ lb, unsigned long long* bytes) {
     __shared__ unsigned long long s_max[kLuThreads / 32];
@@ -543,6 +586,11 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
     for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
         const int v = list ? list[i] : (int)i;
         if (alive[v] != 1) continue;  // block-uniform
+        const int h = hv ? (int)hv[v] : h_all;
+        if (only_h && h != only_h) continue;
+        const int64_t M = Mv ? (int64_t)Mv[v] : M_all;
+        const int32_t* lsz_prev = h >= 2 ? lsz + (size_t)(h - 2) * (size_t)n : nullptr;
+        const uint8_t* lk_prev = h >= 2 ? lk + (size_t)(h - 2) * (size_t)n : nullptr;
         unsigned long long m = 0;
         const int64_t b = rowptr[v], e = rowptr[v + 1];
         if (lsz_prev) {
@@ -587,7 +635,7 @@ int table_lg(int64_t M) {
 }
 
 int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
-                 int64_t count_static, int track, cudaStream_t s, int round_mode) {
+                 int64_t count_static, int track, cudaStream_t s, int round_mode, int skip_last) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
     LevelArgs a;
@@ -596,16 +644,16 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.alive = g.alive;
     a.rank = g.rank;
     a.n = g.n;
-    a.level = level;
-    a.last = level == g.h;
+    a.level = round_mode == 2 ? 0 : level;  // the refine computes each node's last level
+    a.h = g.h;
+    a.hv = g.hv;
+    a.skip_last = skip_last < 0 ? (round_mode == 1 ? 1 : 0) : skip_last;
     a.M = g.M;
+    a.Mv = g.Mv;
     a.cap = g.cap;
-    a.keys_in = level >= 2 ? g.keys + (size_t)(level - 2) * (size_t)g.n * (size_t)g.cap : nullptr;
-    a.keys_out = level < g.h ? g.keys + (size_t)(level - 1) * (size_t)g.n * (size_t)g.cap : nullptr;
-    a.lsz_in = level >= 2 ? g.lsz + (size_t)(level - 2) * g.n : nullptr;
-    a.lk_in = level >= 2 ? g.lk + (size_t)(level - 2) * g.n : nullptr;
-    a.lsz_out = g.lsz + (size_t)(level - 1) * g.n;
-    a.lk_out = g.lk + (size_t)(level - 1) * g.n;
+    a.keys = g.keys;
+    a.lsz = g.lsz;
+    a.lk = g.lk;
     a.est = g.d64;
     a.worklist = worklist;
     a.d_count = d_count;
@@ -635,7 +683,10 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_changed");
     }
     const int64_t work = worklist ? g.n : count_static;
-    if (level == 1) {
+    // which kernels can have nodes to do: level 1 (warp per node) and/or >= 2 (CTA per node)
+    const bool want1 = round_mode == 2 ? g.hmin == 1 : level == 1;
+    const bool wantU = round_mode == 2 ? g.hmax >= 2 : level >= 2;
+    if (want1) {
         a.bytes = &g.state->bytes[kProfLevel1];
         if (round_mode == 0) {
             e = cudaMemsetAsync(a.n_heavy, 0, sizeof(int), s);
@@ -650,8 +701,8 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
         k_level1_heavy<<<g.ctx->sm_count * 2, kL1Threads, 0, s>>>(a);
         count_launch(g, 2);
         prof_end(g, kProfLevel1, s);
-        return KH_OK;
     }
+    if (!wantU) return KH_OK;
     a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
     const size_t dyn = levelU_smem(lg);
@@ -686,15 +737,32 @@ void launch_mark_neighbours(Graph& g, const int* list1, const int* cnt1, const i
     prof_end(g, kProfFrontier, s);
 }
 
-void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s) {
+// lvl_out[v] = k[v, h(v)], bs_out[v] = |B[v, h(v)]| (each node's last level)
+__global__ void k_gather_last(int64_t n, int h_all, const uint8_t* __restrict__ hv,
+                              const int32_t* __restrict__ lsz, const uint8_t* __restrict__ lk,
+                              uint8_t* __restrict__ lvl_out, int32_t* __restrict__ bs_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int h = hv ? (int)hv[v] : h_all;
+        const size_t at = (size_t)(h - 1) * (size_t)n + (size_t)v;
+        if (lvl_out) lvl_out[v] = lk[at];
+        if (bs_out) bs_out[v] = lsz[at];
+    }
+}
+
+void launch_gather_last(Graph& g, uint8_t* lvl_out, int32_t* bs_out, cudaStream_t s) {
+    if (g.n == 0) return;
+    k_gather_last<<<g.ctx->sm_count * 4, 256, 0, s>>>(g.n, g.h, g.hv, g.lsz, g.lk, lvl_out, bs_out);
+    count_launch(g, 1);
+}
+
+void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStream_t s, int only_h) {
     if (g.n == 0) return;
     const int grid = g.ctx->sm_count * 8;
-    const int32_t* lsz_prev = g.h >= 2 ? g.lsz + (size_t)(g.h - 2) * g.n : nullptr;
-    const uint8_t* lk_prev = g.h >= 2 ? g.lk + (size_t)(g.h - 2) * g.n : nullptr;
     prof_begin(g, kProfFrontier, s);
-    k_stale_sampled<<<grid, kLuThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.rank, lsz_prev, lk_prev, g.M,
-                                         list, d_count, g.n, g.fresh, g.lb64,
-                                         &g.state->bytes[kProfFrontier]);
+    k_stale_sampled<<<grid, kLuThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.rank, g.lsz, g.lk, g.h,
+                                                g.hv, g.M, g.Mv, only_h, list, d_count, g.n,
+                                                g.fresh, g.lb64, &g.state->bytes[kProfFrontier]);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

@@ -44,6 +44,7 @@ SIGNATURES = [
     ("kh_last_error", ctypes.c_char_p, [_P]),
     ("kh_graph_load_csr", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _PP]),
     ("kh_graph_free", ctypes.c_int, [_P]),
+    ("kh_graph_load_batch", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_uint32, _PP]),
     ("kh_graph_n", ctypes.c_int, [_P, _I64P]),
     ("kh_set_h", ctypes.c_int, [_P, ctypes.c_int32]),
     ("kh_set_sampling", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
@@ -313,3 +314,24 @@ def kh_hdegree_exact_noalloc(rowptr, col, h: int, deg, stream=None) -> int:
     return int(load().kh_hdegree_exact_noalloc(n, ctypes.c_void_p(rowptr.data_ptr()),
                                                ctypes.c_void_p(col.data_ptr()), h,
                                                ctypes.c_void_p(deg.data_ptr()), s))
+
+
+def kh_graph_load_batch(ctx: Ctx, vtx_off, rowptr, col, h_per_graph=None) -> Graph:
+    """Packed graphs (see include/khcore.h): vtx_off int64[g+1] and h_per_graph
+    int32[g] on the host; rowptr/col numpy (host) or torch CUDA tensors."""
+    vtx_off = np.ascontiguousarray(vtx_off, dtype=np.int64)
+    hpg = None if h_per_graph is None else np.ascontiguousarray(h_per_graph, dtype=np.int32)
+    if _is_torch(rowptr):
+        import torch
+        assert rowptr.dtype == torch.int64 and col.dtype == torch.int32
+    else:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+    pr, dev = _ptr(rowptr)
+    pc, _ = _ptr(col)
+    h = ctypes.c_void_p()
+    rc = load().kh_graph_load_batch(ctx.handle, int(vtx_off.size - 1), _ptr(vtx_off)[0], pr, pc,
+                                    _ptr(hpg)[0] if hpg is not None else None,
+                                    KH_DEVICE_PTR if dev else 0, ctypes.byref(h))
+    _check(rc, ctx)
+    return Graph(ctx, h, int(vtx_off[-1]))
