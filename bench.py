@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
                                     "sampled3", "exact2"],
                    help="run one operation of the step once (a target for profilers) and exit")
+    p.add_argument("--workload", choices=["chung_lu", "batch"], default="chung_lu",
+                   help="batch: 4096 preferential-attachment graphs, batched vs one graph per launch")
+    p.add_argument("--batch-graphs", type=int, default=4096)
+    p.add_argument("--exact-graphs", type=int, default=512)
     return p.parse_args()
 
 
@@ -389,10 +393,93 @@ def run_op(args):
     ctx.close()
 
 
+def run_batch(args):
+    """Batched workload: many preferential-attachment graphs (n log-uniform in
+    [100, 20000], m uniform in {3..8}, h uniform in {2,3,4}, per-graph M).
+
+    The plain form loads and peels one graph per call; the batched form peels
+    all graphs from one packed CSR, each graph with its own h, M and core value
+    (kh_graph_load_batch).  Both are timed in full on every graph, and the
+    batched results must equal the per-graph ones bit for bit.
+      sampled: Core (Alg. 4) on all graphs at their own h;
+      exact:   ExactCore at h = 2 on the first --exact-graphs graphs (exact
+               peels at h = 3, 4 of these graphs are the O(n^2 m) regime the
+               paper's sampling exists to avoid; see the design notes)."""
+    import torch
+    from paper_2112_06154_gb300 import graphgen as gg
+    from paper_2112_06154_gb300 import khcore as K
+    K.load(build_if_missing=True)
+    G = args.batch_graphs
+    t0 = time.perf_counter()
+    vtx_off, rp, cl, hs = gg.ba_batch_workload(G)
+    gen_s = time.perf_counter() - t0
+    n = int(vtx_off[-1])
+    ctx = K.kh_ctx_create(0)
+
+    def sub(q):
+        a, b = int(vtx_off[q]), int(vtx_off[q + 1])
+        return rp[a:b + 1] - rp[a], cl[rp[a]:rp[b]] - a
+
+    def batched(vo, rpb, clb, hpg, fn, force_h=None):
+        B = K.kh_graph_load_batch(ctx, vo, rpb, clb, hpg)
+        if force_h:
+            K.kh_set_h(B, force_h)
+        fn(B)  # warm-up: allocation and graph capture
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn(B)
+        dt = time.perf_counter() - t
+        _, rounds, upd = K.kh_peel_info(B, False)
+        B.close()
+        return out, dt, rounds, upd
+
+    def alone(qs, fn, force_h=None):
+        outs = []
+        t = time.perf_counter()
+        for q in qs:
+            Gq = K.kh_graph_load_csr(ctx, *sub(q))
+            K.kh_set_h(Gq, int(force_h or hs[q]))
+            K.kh_set_sampling(Gq, seed=1, M=0, eps=EPS, delta=DELTA)
+            outs.append(fn(Gq))
+            Gq.close()
+        return outs, time.perf_counter() - t
+
+    # sampled, every graph at its own h
+    cs, t_bs, r_bs, u_bs = batched(vtx_off, rp, cl, hs, K.kh_core_sampled)
+    outs, t_as = alone(range(G), K.kh_core_sampled)
+    same_s = all((o == cs[vtx_off[q]:vtx_off[q + 1]]).all() for q, o in enumerate(outs))
+    # exact at h = 2 on a sub-batch
+    GE = min(args.exact_graphs, G)
+    vo_e = vtx_off[:GE + 1]
+    rp_e = rp[:int(vo_e[-1]) + 1]
+    cl_e = cl[:int(rp_e[-1])]
+    ce, t_be, r_be, u_be = batched(vo_e, rp_e, cl_e, hs[:GE], K.kh_core_exact, force_h=2)
+    oute, t_ae = alone(range(GE), K.kh_core_exact, force_h=2)
+    same_e = all((o == ce[vtx_off[q]:vtx_off[q + 1]]).all() for q, o in enumerate(oute))
+    line = {
+        "workload": f"batch_ba{G}", "impl": "ours",
+        "metric": "(k,h)-core decompositions of a batch of graphs: batched vs one graph per call",
+        "unit": "s", "higher_is_better": False,
+        "graphs": G, "n": n, "m": int(cl.size // 2), "h_counts": np.bincount(hs, minlength=5)[2:].tolist(),
+        "generation_s": round(gen_s, 1),
+        "sampled": {"batched_s": t_bs, "one_graph_per_call_s": t_as, "speedup": t_as / t_bs,
+                    "rounds": r_bs, "updates": u_bs, "identical": bool(same_s)},
+        "exact_h2": {"graphs": GE, "batched_s": t_be, "one_graph_per_call_s": t_ae,
+                     "speedup": t_ae / t_be, "rounds": r_be, "updates": u_be,
+                     "identical": bool(same_e)},
+        "timing": "wall clock around the call (host outputs); one-graph-per-call includes each "
+                  "graph's load, as a caller without batching pays it",
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.op:
         run_op(args)
+    elif args.workload == "batch" and args.impl == "ours":
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -69,6 +69,11 @@ int ensure_work(Graph& g) {
     if ((rc = dalloc(g.ctx, &g.deadbm, ((n + 127) / 128) * 4, "deadbm"))) return rc;
     if ((rc = dalloc(g.ctx, &g.degX, n, "degX"))) return rc;
     if ((rc = dalloc(g.ctx, &g.lb64, n, "lb64"))) return rc;
+    const size_t ng = (size_t)(g.gid ? g.ngraphs : 1);
+    if ((rc = dalloc(g.ctx, &g.pc, ng, "per-graph c"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.pmn, ng, "per-graph minimum"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.pmu, ng, "per-graph threshold"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.pleft, ng, "per-graph alive count"))) return rc;
     return KH_OK;
 }
 
@@ -204,6 +209,10 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.deadbm);
     dfree(&g.gid);
     dfree(&g.vtx_off);
+    dfree(&g.pc);
+    dfree(&g.pmn);
+    dfree(&g.pmu);
+    dfree(&g.pleft);
     dfree(&g.hv);
     dfree(&g.Mv);
     delete g.h_vtx_off;

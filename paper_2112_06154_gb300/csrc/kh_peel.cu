@@ -37,6 +37,7 @@
 // graph holds kRoundsPerGraph rounds; rounds that start with no alive node do
 // nothing.  The host replays the graph and reads the state once per replay.
 #include <cstring>
+#include <vector>
 
 #include "kh_internal.cuh"
 
@@ -48,17 +49,42 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kPeelThreads = 256;
 constexpr int kRoundsPerGraph = 8;
 
+// Per-graph peel state (a single graph has one entry; a batch one per graph,
+// so each graph peels with its own c exactly as it would alone):
+//   c[g]   core value reached so far, mn[g] this round's minimum of d,
+//   mu[g]  this round's minimum of the upper bounds (lazy refine threshold).
+struct PeelState {
+    unsigned long long* c;
+    unsigned long long* mn;
+    unsigned long long* mu;
+    int32_t* left;       // alive nodes per graph (batches: per-graph early stop)
+    const int32_t* gid;  // graph of each node; nullptr for a single graph
+};
+
+__device__ __forceinline__ int graph_of(const PeelState& p, int64_t v) {
+    return p.gid ? p.gid[v] : 0;
+}
+
+// Minimum of x over a node set into target[graph]: a single graph reduces
+// per block; a batch takes one atomic per node that improves its graph's
+// current minimum (read first, so most nodes need none).
 template <typename T>
 __global__ void k_min_alive(const uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
-                            DevState* st, unsigned long long* target) {
+                            DevState* st, unsigned long long* target, const int32_t* __restrict__ gid) {
     if (st->n_alive == 0) return;
     unsigned long long m = ~0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
         if (alive[v] == 1) {
             const unsigned long long x = (unsigned long long)d[v];
-            if (x < m) m = x;
+            if (gid) {
+                const int g = gid[v];
+                if (x < *(volatile unsigned long long*)(target + g)) atomicMin(target + g, x);
+            } else if (x < m) {
+                m = x;
+            }
         }
+    if (gid) return;
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o = __shfl_down_sync(kFull, m, off);
         if (o < m) m = o;
@@ -82,34 +108,43 @@ struct LbArgs {
 __device__ __forceinline__ unsigned long long lower_bound(const LbArgs& a, int v) { return a.lb[v]; }
 
 __global__ void k_min_lb(const uint8_t* __restrict__ alive, const uint8_t* __restrict__ fresh,
-                         int64_t n, LbArgs a, DevState* st) {
+                         int64_t n, LbArgs a, DevState* st, PeelState p) {
     if (st->n_alive == 0) return;
     unsigned long long m = ~0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
         if (alive[v] == 1 && !fresh[v]) {
             const unsigned long long x = lower_bound(a, (int)v);
-            if (x < m) m = x;
+            if (p.gid) {
+                const int g = p.gid[v];
+                if (x < *(volatile unsigned long long*)(p.mu + g)) atomicMin(p.mu + g, x);
+            } else if (x < m) {
+                m = x;
+            }
         }
+    if (p.gid) return;
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long o = __shfl_down_sync(kFull, m, off);
         if (o < m) m = o;
     }
-    if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(&st->minU, m);
+    if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(p.mu, m);
 }
 
 // Stale nodes with lb <= T = max(c, U) join the refine list and become fresh
 // (their value is recomputed right after, before anything reads it).
 __global__ void k_collect(const uint8_t* __restrict__ alive, uint8_t* __restrict__ fresh, int64_t n,
-                          LbArgs a, DevState* st, int32_t* __restrict__ out) {
+                          LbArgs a, DevState* st, PeelState p, int32_t* __restrict__ out) {
     if (st->n_alive == 0) return;
-    const unsigned long long T = st->c > st->minU ? st->c : st->minU;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
         bool due = false;
-        if (v < n && alive[v] == 1 && !fresh[v]) due = lower_bound(a, (int)v) <= T;
+        if (v < n && alive[v] == 1 && !fresh[v]) {
+            const int g = graph_of(p, v);
+            const unsigned long long T = p.c[g] > p.mu[g] ? p.c[g] : p.mu[g];
+            due = lower_bound(a, (int)v) <= T;
+        }
         const uint32_t m = __ballot_sync(kFull, due);
         int base = 0;
         if (lane == 0 && m) base = atomicAdd(&st->nQ, __popc(m));
@@ -132,10 +167,9 @@ __global__ void k_init_exact(const int64_t* __restrict__ rowptr, int64_t n, int3
 
 template <typename T, typename C>
 __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
-                         DevState* st, C* __restrict__ core, int32_t* __restrict__ round_of,
+                         DevState* st, PeelState p, C* __restrict__ core, int32_t* __restrict__ round_of,
                          int32_t* __restrict__ R, int32_t* __restrict__ seen) {
     if (st->n_alive == 0) return;
-    const unsigned long long c = st->c > st->minval ? st->c : st->minval;
     const int round = st->round;
     const int lane = threadIdx.x & 31;
     int keep = 0;
@@ -144,8 +178,11 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
         bool rm = false;
         if (v < n && alive[v] == 1) {
+            const int g = graph_of(p, v);
+            const unsigned long long c = p.c[g] > p.mn[g] ? p.c[g] : p.mn[g];
             if ((unsigned long long)d[v] <= c) {
                 rm = true;
+                if (p.gid) atomicSub(p.left + g, 1);
                 core[v] = (C)c;
                 round_of[v] = round;
                 alive[v] = 2;
@@ -170,10 +207,11 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
 // c in round `round + 1`.  Every block evaluates the condition; block 0
 // records it for the kernels that follow (they skip the refresh).
 template <typename C>
-__global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* st,
+__global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* st, PeelState p,
                               C* __restrict__ core, int32_t* __restrict__ round_of) {
     if (st->n_alive == 0) return;
-    const unsigned long long c = st->c > st->minval ? st->c : st->minval;
+    // single graphs only (a batch has no global early stop)
+    const unsigned long long c = p.c[0] > p.mn[0] ? p.c[0] : p.mn[0];
     const int left = st->n_alive_next;
     const bool early = left > 0 && c + 1 >= (unsigned long long)left;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->early = early ? 1 : 0;
@@ -188,10 +226,36 @@ __global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* 
         }
 }
 
+// Batches: the early stop of each graph on its own (c_g >= |X_g| - 1 after
+// this round's removal).  Finished graphs' nodes leave at once, so the
+// refresh that follows never reaches them.
+template <typename C>
+__global__ void k_assign_rest_batch(uint8_t* __restrict__ alive, int64_t n, DevState* st,
+                                    PeelState p, C* __restrict__ core, int32_t* __restrict__ round_of) {
+    if (st->n_alive == 0) return;
+    const int round = st->round + 1;
+    int gone = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (alive[v] == 1) {
+            const int g = p.gid[v];
+            const unsigned long long c = p.c[g] > p.mn[g] ? p.c[g] : p.mn[g];
+            const int left = *(volatile int32_t*)(p.left + g);
+            if (left > 0 && c + 1 >= (unsigned long long)left) {
+                core[v] = (C)c;
+                round_of[v] = round;
+                alive[v] = 0;
+                ++gone;
+            }
+        }
+    for (int off = 16; off > 0; off >>= 1) gone += __shfl_down_sync(kFull, gone, off);
+    if ((threadIdx.x & 31) == 0 && gone) atomicSub(&st->n_alive_next, gone);
+}
+
 // Ends a round: removed nodes leave (alive = 0, dead bitmap bit set); the
 // last block to finish advances the state and zeroes the per-round counters.
 __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict__ R, DevState* st,
-                         uint32_t* __restrict__ deadbm) {
+                         uint32_t* __restrict__ deadbm, PeelState p, int64_t ngraphs) {
     __shared__ int s_last;
     const int nR = st->nR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -209,14 +273,17 @@ __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict_
     if (!s_last) return;
     __threadfence();
     for (int i = threadIdx.x; i < kRcCount; i += blockDim.x) st->rc[i] = 0;
+    // every graph: c = max(c, this round's minimum); minima reset
+    for (int64_t q = threadIdx.x; q < ngraphs; q += blockDim.x) {
+        if (p.mn[q] != ~0ull && p.mn[q] > p.c[q]) p.c[q] = p.mn[q];
+        p.mn[q] = ~0ull;
+        p.mu[q] = ~0ull;
+    }
     if (threadIdx.x == 0) {
         if (st->n_alive != 0) {
-            if (st->minval > st->c && st->minval != ~0ull) st->c = st->minval;
             st->round += st->early ? 2 : 1;
             st->n_alive = st->early ? 0 : st->n_alive_next;
         }
-        st->minval = ~0ull;
-        st->minU = ~0ull;
         st->n_alive_next = 0;
         st->nR = 0;
         st->nQ = 0;
@@ -238,12 +305,24 @@ LbArgs lb_args(const Graph& g) {
     return a;
 }
 
+PeelState peel_state(const Graph& g) {
+    PeelState p;
+    p.c = g.pc;
+    p.mn = g.pmn;
+    p.mu = g.pmu;
+    p.left = g.pleft;
+    p.gid = g.gid;
+    return p;
+}
+
+int64_t peel_graphs(const Graph& g) { return g.gid ? g.ngraphs : 1; }
+
 // Recompute the last level of the refine list (stale nodes with lb <= T).
 int refine(Graph& g, bool sampled, cudaStream_t s) {
     const int grid = peel_grid(g);
     const LbArgs la = lb_args(g);
     prof_begin(g, kProfPeel, s);
-    k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state, g.listB);
+    k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state, peel_state(g), g.listB);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s, 2);
@@ -269,16 +348,14 @@ int start_peel(Graph& g, bool sampled, cudaStream_t s) {
         launch_stale_exact(g, nullptr, nullptr, s);
     }
     const LbArgs la = lb_args(g);
-    k_min_lb<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state);
+    k_min_lb<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state, peel_state(g));
     count_launch(g, 1);
     rc = refine(g, sampled, s);
     if (rc) return rc;
     // the bootstrap used the per-round counters: zero them for round 0
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.state->rc, 0, sizeof(int) * kRcCount, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->nQ, 0, sizeof(int), s));
-    const unsigned long long all1 = ~0ull;
-    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&g.state->minU, &all1, sizeof(all1), cudaMemcpyHostToDevice, s));
-    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // keeps `all1` alive until copied
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmu, 0xff, sizeof(unsigned long long) * peel_graphs(g), s));
     return KH_OK;
 }
 
@@ -290,29 +367,35 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     prof_begin(g, kProfPeel, s);
     if (sampled)
         k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
-                                                                      &g.state->minU);
+                                                                      g.pmu, g.gid);
     else
-        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state,
-                                                           &g.state->minU);
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state, g.pmu,
+                                                           g.gid);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     rc = refine(g, sampled, s);
     if (rc) return rc;
     prof_begin(g, kProfPeel, s);
+    const PeelState ps = peel_state(g);
     if (sampled) {
         k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
-                                                                      &g.state->minval);
+                                                                      g.pmn, g.gid);
         k_select<unsigned long long, unsigned long long><<<grid, kPeelThreads, 0, s>>>(
-            g.alive, g.d64, g.n, g.state, g.core64, g.round_of, g.listR, g.seen);
+            g.alive, g.d64, g.n, g.state, ps, g.core64, g.round_of, g.listR, g.seen);
         count_launch(g, 2);
     } else {
-        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state,
-                                                           &g.state->minval);
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state, g.pmn,
+                                                           g.gid);
         k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
-            g.alive, g.d32, g.n, g.state, g.core32, g.round_of, g.listR, g.seen);
-        k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, g.core32,
-                                                             g.round_of);
-        count_launch(g, 3);
+            g.alive, g.d32, g.n, g.state, ps, g.core32, g.round_of, g.listR, g.seen);
+        count_launch(g, 2);
+        if (!g.gid)  // the early stop of Sec. 5
+            k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, ps, g.core32,
+                                                                 g.round_of);
+        else  // the same, graph by graph
+            k_assign_rest_batch<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, ps,
+                                                                       g.core32, g.round_of);
+        count_launch(g, 1);
     }
     prof_end(g, kProfPeel, s);
     if (!sampled) {
@@ -334,7 +417,7 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
         if (rc) return rc;
     }
     prof_begin(g, kProfPeel, s);
-    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm);
+    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm, ps, peel_graphs(g));
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     return KH_OK;
@@ -429,6 +512,19 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     init.n_alive = (int)g.n;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.state, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // `init` is a host stack object
+    const size_t pbytes = sizeof(unsigned long long) * (size_t)peel_graphs(g);
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pc, 0, pbytes, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmn, 0xff, pbytes, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmu, 0xff, pbytes, s));
+    if (g.gid) {
+        // alive nodes per graph start at the graph sizes
+        std::vector<int32_t> sizes((size_t)g.ngraphs);
+        for (int64_t q = 0; q < g.ngraphs; ++q)
+            sizes[(size_t)q] = (int32_t)((*g.h_vtx_off)[q + 1] - (*g.h_vtx_off)[q]);
+        KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.pleft, sizes.data(), sizeof(int32_t) * sizes.size(),
+                                           cudaMemcpyHostToDevice, s));
+        KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // `sizes` is a host vector
+    }
     rc = start_peel(g, sampled, s);
     if (rc) return rc;
     // the BFS scratch must exist before capture (its allocation may synchronize)

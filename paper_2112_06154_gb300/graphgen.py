@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "csr_from_edges", "erdos_renyi", "chung_lu", "rmat", "barabasi_albert",
     "grid", "complete", "path", "cycle", "star", "random_small",
-    "pack_batch", "graph_stats",
+    "pack_batch", "graph_stats", "barabasi_albert_batch", "ba_batch_workload",
 ]
 
 
@@ -256,3 +256,79 @@ def graph_stats(rowptr, col):
         "sum_deg2": int((deg.astype(np.int64) ** 2).sum()),
         "isolated": int((deg == 0).sum()),
     }
+
+
+def barabasi_albert_batch(ns, ms, seed: int):
+    """Many preferential-attachment graphs (copy model, as in barabasi_albert)
+    drawn in one vectorised pass and packed as in pack_batch.
+
+    Graph q has ns[q] > ms[q] + 1 nodes: a seed clique on ms[q] + 1 nodes, then
+    every later node attaches ms[q] edges whose targets are uniformly drawn
+    entries of the endpoint list of the graph's earlier edges.  Returns
+    (vtx_off int64[g+1], rowptr int64[N+1], col int32[...])."""
+    rng = np.random.default_rng(seed)
+    ns = np.asarray(ns, dtype=np.int64)
+    ms = np.asarray(ms, dtype=np.int64)
+    if np.any(ns <= ms + 1):
+        raise ValueError("every graph needs n > m + 1")
+    G = ns.size
+    vtx_off = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(ns, out=vtx_off[1:])
+    e0 = ms * (ms + 1) // 2                       # seed-clique edges
+    enew = (ns - ms - 1) * ms                     # attachment edges
+    eq = e0 + enew
+    ebase = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(eq, out=ebase[1:])
+    etot = int(ebase[-1])
+    src = np.empty(etot, dtype=np.int64)
+    tgt = np.empty(etot, dtype=np.int64)
+    ptr = np.full(etot, -1, dtype=np.int64)
+    # seed cliques (graph-local ids shifted to global)
+    for q in range(G):
+        cu, cv = np.triu_indices(int(ms[q]) + 1, k=1)
+        a = int(ebase[q])
+        src[a:a + cu.size] = cu + vtx_off[q]
+        tgt[a:a + cu.size] = cv + vtx_off[q]
+    # attachment edges: graph, local node t, and the endpoint they copy
+    gq = np.repeat(np.arange(G), enew)
+    newbase = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(enew, out=newbase[1:])
+    idx = np.arange(int(newbase[-1]), dtype=np.int64) - newbase[gq]
+    mq = ms[gq]
+    t = mq + 1 + idx // mq
+    eid = ebase[gq] + e0[gq] + idx                # global id of the edge itself
+    src[eid] = vtx_off[gq] + t
+    limit = 2 * (e0[gq] + (t - mq - 1) * mq)
+    pick = (rng.random(idx.size) * limit).astype(np.int64)
+    ref = ebase[gq] + (pick >> 1)                 # referenced (earlier) edge
+    side = pick & 1
+    direct = side == 0
+    tgt[eid[direct]] = src[ref[direct]]
+    seedref = (~direct) & ((pick >> 1) < e0[gq])
+    tgt[eid[seedref]] = tgt[ref[seedref]]
+    pend = (~direct) & ~seedref
+    ptr[eid[pend]] = ref[pend]
+    for _ in range(64):
+        todo = np.nonzero(ptr >= 0)[0]
+        if todo.size == 0:
+            break
+        p = ptr[todo]
+        nxt = ptr[p]
+        done = nxt < 0
+        tgt[todo[done]] = tgt[p[done]]
+        ptr[todo] = nxt
+    n = int(vtx_off[-1])
+    rowptr, col = csr_from_edges(n, src, tgt)
+    return vtx_off, rowptr, col
+
+
+def ba_batch_workload(num_graphs: int = 4096, seed: int = 1004, n_lo: int = 100, n_hi: int = 20000):
+    """The batched workload: num_graphs preferential-attachment graphs with n
+    log-uniform in [n_lo, n_hi], attachment m uniform in {3..8} and h uniform
+    in {2, 3, 4}.  Returns (vtx_off, rowptr, col, h_per_graph)."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(n_lo), np.log(n_hi), num_graphs)).round().astype(np.int64)
+    ms = rng.integers(3, 9, num_graphs)
+    hs = rng.integers(2, 5, num_graphs).astype(np.int32)
+    vtx_off, rowptr, col = barabasi_albert_batch(ns, ms, seed + 1)
+    return vtx_off, rowptr, col, hs
