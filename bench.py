@@ -51,8 +51,14 @@ def parse():
     p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
                                     "sampled3", "exact2"],
                    help="run one operation of the step once (a target for profilers) and exit")
-    p.add_argument("--workload", choices=["chung_lu", "batch"], default="chung_lu",
-                   help="batch: 4096 preferential-attachment graphs, batched vs one graph per launch")
+    p.add_argument("--workload", choices=["chung_lu", "batch", "serve"], default="chung_lu",
+                   help="batch: 4096 preferential-attachment graphs, batched vs one graph per call; "
+                        "serve: a Poisson request stream through the continuous-batching server")
+    p.add_argument("--requests", type=int, default=300)
+    p.add_argument("--rate", type=float, default=200.0)
+    p.add_argument("--pool", type=int, default=24)
+    p.add_argument("--n-max", type=int, default=100_000)
+    p.add_argument("--slots", type=int, default=4)
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--exact-graphs", type=int, default=512)
     return p.parse_args()
@@ -151,6 +157,20 @@ def profile_traffic(kind_name):
     except OSError:
         pass
     return None
+
+
+def aggregate_ranks(ms, updates, world, device):
+    """Replicas: the slowest rank's time and the updates of all ranks."""
+    if world <= 1:
+        return ms, updates
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, updates], dtype=torch.float64, device=device)
+    mx = t[0:1].clone()
+    sm = t[1:2].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
 
 
 # ----------------------------------------------------------------- our arm
@@ -290,16 +310,7 @@ def run_ours(args):
                                 "GBps": round(v["alg_bytes"] / 1e6 / v["ms"], 1) if v["ms"] else 0}
                             for k, v in prof.items()}}
 
-    # max over ranks
-    per_rank = torch.tensor([total_ms, float(total_updates)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        t = per_rank.clone()
-        dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        total_ms_max, updates_all = float(t[0]), float(t[1])
-    else:
-        total_ms_max, updates_all = total_ms, float(total_updates)
+    total_ms_max, updates_all = aggregate_ranks(total_ms, float(total_updates), world, "cuda")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -474,10 +485,76 @@ def run_batch(args):
     ctx.close()
 
 
+def serve_pool(count, n_max, seed):
+    """Request graphs: half Chung-Lu (n log-uniform in [1000, n_max], mean degree
+    uniform in [4, 32], exponent uniform in [2.1, 3.0], maximum expected degree
+    sqrt(n * mean degree)), half 2-D grids with 1% shortcut edges (side chosen
+    so that n is log-uniform in the same range)."""
+    from paper_2112_06154_gb300 import graphgen as gg
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(1000), np.log(n_max))))
+        if i % 2 == 0:
+            avg = rng.uniform(4, 32)
+            gam = rng.uniform(2.1, 3.0)
+            pool.append(gg.chung_lu(n, avg, gam, int(np.sqrt(n * avg)), seed + i))
+        else:
+            a = int(np.sqrt(n))
+            pool.append(gg.grid(a, max(n // a, 2), 0.01, seed + i))
+    return pool
+
+
+def run_serve(args):
+    """Poisson request stream (rate req/s) of sampled (k,h)-core decompositions,
+    h uniform in {2, 3, 4}, through the continuous-batching server with
+    --slots concurrent requests, against the same stream with one slot."""
+    from paper_2112_06154_gb300 import serve as S
+    pool = serve_pool(args.pool, args.n_max, 1005)
+    rng = np.random.default_rng(1006)
+    gaps = rng.exponential(1.0 / args.rate, args.requests)
+    picks = rng.integers(0, len(pool), args.requests)
+    hs_r = rng.integers(2, 5, args.requests)
+    out = {}
+    for slots in sorted({args.slots, 1}, reverse=True):
+        srv = S.KhServer(S.gpu_runner(0), slots=slots, mem_budget=96 << 30)
+        rp0, cl0 = pool[0]
+        srv.submit(rp0, cl0, 2).result()  # warm-up: library load, first allocations
+        srv.done.clear()
+        t0 = time.perf_counter()
+        futs = []
+        due = t0
+        for i in range(args.requests):
+            due += gaps[i]
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+            rp, cl = pool[picks[i]]
+            futs.append(srv.submit(rp, cl, int(hs_r[i]), arrival=due))
+        for f in futs:
+            f.result()
+        srv.close()
+        out[f"slots{slots}"] = srv.latency_stats()
+    line = {
+        "workload": "serve_poisson", "impl": "ours",
+        "metric": "sampled (k,h)-core serving: p50/p99 latency and throughput",
+        "requests": args.requests, "rate_rps": args.rate, "pool_graphs": len(pool),
+        "n_range": [1000, args.n_max],
+        "pool_nodes_mean": float(np.mean([p[0].size - 1 for p in pool])),
+        "results": out,
+        "throughput_gain": (out[f"slots{args.slots}"]["throughput_rps"] /
+                            out["slots1"]["throughput_rps"]) if args.slots != 1 else 1.0,
+        "unit": "s", "higher_is_better": False,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.op:
         run_op(args)
+    elif args.workload == "serve" and args.impl == "ours":
+        run_serve(args)
     elif args.workload == "batch" and args.impl == "ours":
         run_batch(args)
     elif args.impl == "reference":
