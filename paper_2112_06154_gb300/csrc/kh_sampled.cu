@@ -302,8 +302,11 @@ __device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, i
     return -1;
 }
 
-// Keys one thread loads per step (one 16-byte vector).
+// Keys one thread loads per step (one 16-byte vector); a warp's chunk.
 constexpr int kKeysPerLane = 4;
+constexpr int kChunkKeys = 32 * kKeysPerLane;
+// Nodes up to this degree use the flat (list, chunk) schedule of k_levelU.
+constexpr int kFlatMax = kLuThreads;
 
 // Shared memory of k_levelU for a table of 2^lg slots: keys, compaction
 // stage (half size), and the list of used slots (16-bit indices).
@@ -320,7 +323,17 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     uint16_t* used = reinterpret_cast<uint16_t*>(s_dyn + hcap + (hcap >> 1));  // hcap slots
     __shared__ int s_hist[32];
     __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
+    // flat mode (degree <= kFlatMax): per neighbour list its node, size, first
+    // chunk index (exclusive prefix of 128-key chunk counts) and the first
+    // chunk that showed a key below t (INT_MAX while none has)
+    __shared__ int32_t s_w[kFlatMax];
+    __shared__ int32_t s_sz[kFlatMax];
+    __shared__ int32_t s_off[kFlatMax];
+    __shared__ int32_t s_dead[kFlatMax];
+    __shared__ int s_wsum[kLuThreads / 32];
+    __shared__ int s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kLuThreads / 32;
     const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
     if (total == 0) return;
     unsigned long long my_bytes = 0;
@@ -363,8 +376,38 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             }
         }
         __syncthreads();
-        // G lanes share one neighbour list and read G*4 consecutive keys per
-        // step; G shrinks for high degree so that many lists are open at once
+        // Flat mode, degree <= kFlatMax: every (list, 128-key chunk) pair is one
+        // work item, warps take items in order, one per step, so long and short
+        // lists balance; a list is dropped once a chunk shows a key below t.
+        const bool flat = deg <= kFlatMax;
+        if (flat) {
+            int cnt = 0;
+            if (tid < deg) {
+                const int32_t w = a.col[b + tid];
+                int sz = 0;
+                if (a.alive[w] == 1) sz = min(nl.lsz_in[w], (int)a.cap);
+                s_w[tid] = w;
+                s_sz[tid] = sz;
+                s_dead[tid] = INT_MAX;
+                cnt = (sz + kChunkKeys - 1) / kChunkKeys;
+            }
+            int inc = cnt;  // block-wide exclusive scan of the chunk counts
+            for (int off = 1; off < 32; off <<= 1) {
+                const int x = __shfl_up_sync(kFull, inc, off);
+                if (lane >= off) inc += x;
+            }
+            if (lane == 31) s_wsum[warp] = inc;
+            __syncthreads();
+            int before = 0;
+            for (int w2 = 0; w2 < warp; ++w2) before += s_wsum[w2];
+            if (tid < deg) s_off[tid] = before + inc - cnt;
+            if (tid == kLuThreads - 1) s_total = before + inc;
+            __syncthreads();
+        }
+        int fbase = 0;  // flat mode: first item of this step
+        // Grouped mode (high degree): G lanes share one neighbour list and read
+        // G*4 consecutive keys per step; G shrinks with degree so that many
+        // lists are open at once (hubs: one lane per list)
         int G = 32;
         while (G > 1 && (kLuThreads / G) < deg) G >>= 1;
         const int ngroups = kLuThreads / G;
@@ -376,10 +419,56 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         bool any = true;
         while (any) {
             const int t = *(volatile int*)&s_t;
+            if (flat) {
+                const int c = fbase + warp;
+                if (c < s_total) {
+                    int lo = 0, hi = deg - 1;  // last list whose first chunk is <= c
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_off[mid] <= c) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    // chunks after one with a key below t hold only keys below t;
+                    // warps of one step run unordered, so an earlier chunk of the
+                    // same list is still read even when a later one was seen first
+                    if (c <= __shfl_sync(kFull, s_dead[lo], 0)) {
+                        const int sz = s_sz[lo];
+                        const int p = (c - s_off[lo]) * kChunkKeys + lane * kKeysPerLane;
+                        bool below = false;
+                        if (p < sz) {
+                            const uint4 k4 = *reinterpret_cast<const uint4*>(
+                                nl.keys_in + (size_t)s_w[lo] * (size_t)a.cap + p);
+                            const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+                            for (int q = 0; q < kKeysPerLane; ++q) {
+                                if (p + q < sz) {
+                                    const uint32_t key = kk[q];
+                                    const int r = (int)(key >> kIdBits);
+                                    my_bytes += 4;
+                                    if (r >= t) {
+                                        const int slot = set_insert(tab, lg, key, a.err);
+                                        if (slot >= 0) {
+                                            const int u = atomicAdd(&s_nused, 1);
+                                            if (u < hcap) used[u] = (uint16_t)slot;
+                                            else atomicOr(a.err, kErrProbe);
+                                            atomicAdd(&s_hist[r], 1);
+                                        }
+                                    } else {
+                                        below = true;
+                                    }
+                                }
+                            }
+                        }
+                        // ranks only fall along a list: the rest of it is below t
+                        if (__any_sync(kFull, below) && lane == 0) atomicMin(&s_dead[lo], c);
+                    }
+                }
+                fbase += nwarps;
+            }
             // advance to an alive neighbour with a non-empty list (group-uniform)
             int32_t w = -1;
             int sz = 0;
-            while (li < deg) {
+            while (!flat && li < deg) {
                 w = a.col[b + li];
                 if (a.alive[w] == 1) {
                     sz = min(nl.lsz_in[w], (int)a.cap);
@@ -389,7 +478,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 pos = 0;
             }
             bool below = false;
-            if (li < deg) {
+            if (!flat && li < deg) {
                 const int p = pos + gl * kKeysPerLane;
                 if (p < sz) {
                     const uint4 k4 =
@@ -417,7 +506,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
             }
             const uint32_t bal = __ballot_sync(kFull, below);
-            if (li < deg) {
+            if (!flat && li < deg) {
                 if ((bal & gmask) || pos + step >= sz) {
                     li += ngroups;
                     pos = 0;
@@ -425,7 +514,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                     pos += step;
                 }
             }
-            any = __syncthreads_or(li < deg);
+            any = __syncthreads_or(flat ? fbase < s_total : li < deg);
             if (warp == 0) {
                 // smallest level >= t with at most M distinct members (Alg. 5's
                 // trim): lane j holds S_j = #{distinct keys with rank >= j}
