@@ -158,6 +158,11 @@ int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updat
 #define KH_PROF_KINDS 5
 int kh_prof_enable(kh_graph *g, int32_t on);
 int kh_prof_read(kh_graph *g, int32_t kind, double *ms, int64_t *launches, double *alg_bytes);
+/* Per-bracket event times of one class since kh_prof_enable(g, 1), in launch
+ * order: the first min(cap, *count) go to ms (host float[cap]); *count is
+ * the number recorded.  KH_EINVAL for a NULL count, a negative cap, or
+ * cap > 0 with a NULL ms. */
+int kh_prof_trace(kh_graph *g, int32_t kind, float *ms, int64_t cap, int64_t *count);
 
 /* Number of CUDA kernels the library has launched for this graph since it was
  * loaded (kernels inside a replayed CUDA graph count one each per replay).

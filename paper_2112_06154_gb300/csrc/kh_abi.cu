@@ -121,6 +121,8 @@ static int prof_collect(Graph& g) {
             const int k = (*g.prof_kind)[i];
             g.prof_ms[k] += ms;
             g.prof_launches[k] += 1;
+            if (!g.prof_trace[k]) g.prof_trace[k] = new std::vector<float>();
+            g.prof_trace[k]->push_back(ms);
         } else {
             cudaGetLastError();
         }
@@ -235,6 +237,10 @@ static void free_graph_arrays(Graph& g) {
     }
     delete g.prof_kind;
     g.prof_kind = nullptr;
+    for (int k = 0; k < kProfKinds; ++k) {
+        delete g.prof_trace[k];
+        g.prof_trace[k] = nullptr;
+    }
 }
 
 static int set_M(Graph& g, int64_t M) {
@@ -671,6 +677,7 @@ int kh_prof_enable(kh_graph* G, int32_t on) {
     for (int k = 0; k < kh::kProfKinds; ++k) {
         g.prof_ms[k] = 0.0;
         g.prof_launches[k] = 0;
+        if (g.prof_trace[k]) g.prof_trace[k]->clear();
     }
     KH_CUDA_TRY(g.ctx, cudaMemset(g.state->bytes, 0, sizeof(g.state->bytes)));
     g.prof_on = on != 0;
@@ -689,6 +696,20 @@ int kh_prof_read(kh_graph* G, int32_t kind, double* ms, int64_t* launches, doubl
     if (ms) *ms = g.prof_ms[kind];
     if (launches) *launches = g.prof_launches[kind];
     if (alg_bytes) *alg_bytes = (double)b;
+    return KH_OK;
+}
+
+int kh_prof_trace(kh_graph* G, int32_t kind, float* ms, int64_t cap, int64_t* count) {
+    if (!G || !count || cap < 0 || (cap > 0 && !ms)) return KH_EINVAL;
+    Graph& g = G->g;
+    if (kind < 0 || kind >= kh::kProfKinds) return kh::set_error(g.ctx, KH_EINVAL, "bad profiling kind");
+    cudaSetDevice(g.ctx->device);
+    int rc = kh::prof_collect(g);
+    if (rc) return rc;
+    const std::vector<float>* t = g.prof_trace[kind];
+    const int64_t total = t ? (int64_t)t->size() : 0;
+    for (int64_t i = 0; i < total && i < cap; ++i) ms[i] = (*t)[(size_t)i];
+    *count = total;
     return KH_OK;
 }
 

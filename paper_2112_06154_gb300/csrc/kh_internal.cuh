@@ -200,6 +200,7 @@ struct Graph {
     std::vector<cudaEvent_t>* prof_ev;  // pairs (start, stop)
     double prof_ms[kProfKinds];
     int64_t prof_launches[kProfKinds];
+    std::vector<float>* prof_trace[kProfKinds];  // per-bracket ms, in launch order
     // cached CUDA graph of a batch of peeling rounds
     cudaGraphExec_t round_exec;
     int round_exec_key[8];

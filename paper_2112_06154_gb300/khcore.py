@@ -60,6 +60,7 @@ SIGNATURES = [
     ("kh_prof_enable", ctypes.c_int, [_P, ctypes.c_int32]),
     ("kh_prof_read", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _I64P,
                                     ctypes.POINTER(ctypes.c_double)]),
+    ("kh_prof_trace", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
     ("kh_sync", ctypes.c_int, [_P]),
@@ -294,6 +295,15 @@ def kh_prof_read(g: Graph, kind: int):
     _check(load().kh_prof_read(g.handle, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
            g.ctx)
     return float(ms.value), int(n.value), float(b.value)
+
+
+def kh_prof_trace(g: Graph, kind: int) -> np.ndarray:
+    """Event time (ms) of every bracketed launch of one kernel class, in order."""
+    n = ctypes.c_int64()
+    _check(load().kh_prof_trace(g.handle, kind, None, 0, ctypes.byref(n)), g.ctx)
+    out = np.zeros(max(n.value, 1), np.float32)
+    _check(load().kh_prof_trace(g.handle, kind, out.ctypes.data, out.size, ctypes.byref(n)), g.ctx)
+    return out[:n.value]
 
 
 def kh_launch_count(g: Graph) -> int:
