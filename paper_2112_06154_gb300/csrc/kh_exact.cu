@@ -111,6 +111,11 @@ struct BfsArgs {
     const int32_t* gid;
     const int64_t* vtx_off;
     const uint8_t* hv;
+    // early stop of the lazy refine (nullptr: every ball is completed)
+    const unsigned long long* stop_c;
+    const unsigned long long* stop_mu;
+    unsigned long long* lb;
+    uint8_t* fresh;
 };
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
@@ -151,6 +156,14 @@ __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q
     }
 }
 
+// Add the lanes' new-vertex counts to the source's shared count (early stop).
+__device__ __forceinline__ void fold_count(int& my, int* s_count, int lane) {
+    int x = my;
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(kFull, x, off);
+    if (lane == 0 && x) atomicAdd(s_count, x);
+    my = 0;
+}
+
 // Expand the row [b, e): lanes take 32 consecutive entries, each warp step
 // issues four independent row loads before visiting (memory-level parallelism).
 template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
@@ -177,7 +190,8 @@ __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32
 template <bool RANKS, bool SMEM, bool ALLALIVE = false>
 __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     extern __shared__ __align__(16) uint32_t s_bm_dyn[];
-    __shared__ int s_src, s_qtail, s_count, s_nheavy;
+    __shared__ int s_src, s_qtail, s_count, s_nheavy, s_stop;
+    __shared__ unsigned long long s_T;
     __shared__ int s_hist[32];
     __shared__ int s_heavy[kMaxHeavy];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -220,11 +234,23 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             q[0] = v;
             s_qtail = 1;
             s_count = 0;
+            s_stop = 0;
+            unsigned long long T = ~0ull;
+            if (a.stop_c) {
+                const int g = a.gid ? a.gid[v] : 0;
+                T = a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g];
+            }
+            s_T = T;
             bm[(v - base) >> 5] |= 1u << ((v - base) & 31);
         }
         if (RANKS && tid < 32) s_hist[tid] = 0;
         __syncthreads();
         int fs = 0, fe = 1, my = 0;
+        // early stop: rows fold their new vertices into s_count as they finish;
+        // once it passes T the remaining rows are skipped (the visited set is a
+        // subset of the ball, so the count is a lower bound of deg_h)
+        const bool can_stop = s_T != ~0ull;
+        const unsigned long long T = s_T;
         for (int d = 0; d < hsrc; ++d) {
             // vertices found at distance d+1 are queued if they will be expanded,
             // or, in global-bitmap mode, so the bitmap can be cleared by a walk
@@ -233,6 +259,14 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             __syncthreads();
             const bool single = (fe - fs) == 1;
             for (int i = fs + warp; i < fe; i += nwarps) {
+                if (can_stop) {
+                    int cnow = 0;
+                    if (lane == 0) cnow = *(volatile int*)&s_count;
+                    if ((unsigned long long)__shfl_sync(kFull, cnow, 0) > T) {
+                        if (lane == 0) s_stop = 1;
+                        break;
+                    }
+                }
                 const int w = q[i];
                 const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
                 if (lane == 0) my_bytes += 8ull + 4ull * (unsigned long long)(e - b);
@@ -251,10 +285,20 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 else
                     expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push,
                                                        lane, my, base);
+                if (can_stop) fold_count(my, &s_count, lane);
             }
             __syncthreads();
             const int nh = min(s_nheavy, kMaxHeavy);
             for (int hi = 0; hi < nh; ++hi) {
+                if (can_stop) {
+                    fold_count(my, &s_count, lane);
+                    int cnow = 0;
+                    if (lane == 0) cnow = *(volatile int*)&s_count;
+                    if ((unsigned long long)__shfl_sync(kFull, cnow, 0) > T) {
+                        if (lane == 0) s_stop = 1;
+                        break;
+                    }
+                }
                 const int w = s_heavy[hi];
                 const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
                 if (seeded)
@@ -265,6 +309,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                                                        4 * blockDim.x, push, lane, my, base);
             }
             __syncthreads();
+            if (s_stop) break;  // d(v) > T: the rest of the ball is not needed
             fs = fe;
             fe = min(s_qtail, (int)a.qcap);
             if (fs >= fe) break;  // nothing new: the ball is complete
@@ -274,7 +319,13 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
         if (lane == 0 && my) atomicAdd(&s_count, my);
         __syncthreads();
         if (tid == 0) {
-            a.deg[v] = s_count;
+            if (s_stop) {
+                // v stays stale: its upper bound is kept, its lower bound raised
+                a.lb[v] = (unsigned long long)s_count;
+                a.fresh[v] = 0;
+            } else {
+                a.deg[v] = s_count;
+            }
             atomicAdd(a.updates, 1ull);
             my_bytes += 4ull + (RANKS ? 4ull * (unsigned long long)a.nj : 0ull);
         }
@@ -424,7 +475,8 @@ void launch_validate(const Graph& g, int* d_err, cudaStream_t s) {
 }
 
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
-                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s, int* round_ctr) {
+                int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s, int* round_ctr,
+                bool early_stop) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
     // batches index the visited bitmap inside the source's graph
@@ -449,7 +501,7 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     const int grid = pick_grid(g.ctx->sm_count, per_sm, work);
     int rc = ensure_bfs_scratch(g, grid, !smem);
     if (rc) return rc;
-    BfsArgs a;
+    BfsArgs a{};
     a.rowptr = g.rowptr;
     a.col = g.col;
     a.alive = g.alive;
@@ -476,6 +528,11 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.gid = g.gid;
     a.vtx_off = g.vtx_off;
     a.hv = g.hv;
+    const bool stop = early_stop && !cnt;
+    a.stop_c = stop ? g.pc : nullptr;
+    a.stop_mu = stop ? g.pmu : nullptr;
+    a.lb = g.lb64;
+    a.fresh = g.fresh;
     if (!round_ctr) {
         e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
@@ -588,7 +645,7 @@ extern "C" int kh_hdegree_exact_noalloc(int64_t n, const int64_t* rowptr, const 
     const int64_t fit = (kNoAllocScratchInts - kNoAllocHeaderInts) / n;  // queues of n entries
     if (grid > fit) grid = fit;
     if (grid > n) grid = n;
-    BfsArgs a;
+    BfsArgs a{};
     memset(&a, 0, sizeof(a));
     a.rowptr = rowptr;
     a.col = col;

@@ -90,9 +90,12 @@ void launch_ranks(const Graph& g, cudaStream_t s);
 void launch_validate(const Graph& g, int* d_err, cudaStream_t s);
 // exact h-degrees of `count` nodes (worklist == nullptr: nodes 0..n-1) into deg32;
 // when cnt != nullptr also the fixed-level counts for j in [jlo, jlo+nj).
+// early_stop (the peel's lazy refine): a source whose partial ball already
+// holds more than T = max(c, mu) of its graph stops and stays stale with that
+// count as its lower bound.
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
                 int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
-                int* round_ctr = nullptr);
+                int* round_ctr = nullptr, bool early_stop = false);
 // one hop of the removed set's ball in the old graph (exact refresh)
 void launch_ball_hop(Graph& g, int hop, cudaStream_t s);
 // exact mode: mark the nodes of `list` (nullptr: all) stale and set their

@@ -327,7 +327,7 @@ int refine(Graph& g, bool sampled, cudaStream_t s) {
     prof_end(g, kProfPeel, s);
     if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s, 2);
     return launch_hdeg(g, g.listB, &g.state->nQ, 0, g.d32, nullptr, 0, 0, s,
-                       &g.state->rc[kRcBfs]);
+                       &g.state->rc[kRcBfs], true);
 }
 
 // Start of a peel: levels below h in full (sampled), every node stale with its

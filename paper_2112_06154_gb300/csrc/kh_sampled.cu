@@ -64,6 +64,14 @@ struct LevelArgs {
     int* err;
     unsigned long long* updates;
     unsigned long long* bytes;
+    // Early stop of the lazy refine: a node whose partial estimate already
+    // exceeds T = max(c, mu) of its graph cannot leave in this round, so it
+    // stays stale with that value as its lower bound (nullptr: no early stop).
+    const unsigned long long* stop_c;
+    const unsigned long long* stop_mu;
+    const int32_t* gid;
+    unsigned long long* lb;
+    uint8_t* fresh;
 };
 
 constexpr int kL1Heavy = 512;
@@ -323,6 +331,8 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     uint16_t* used = reinterpret_cast<uint16_t*>(s_dyn + hcap + (hcap >> 1));  // hcap slots
     __shared__ int s_hist[32];
     __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
+    __shared__ int s_vin, s_exit;                // own key in the table; early stop taken
+    __shared__ unsigned long long s_T, s_part;  // early-stop threshold; partial estimate
     // flat mode (degree <= kFlatMax): per neighbour list its node, size, first
     // chunk index (exclusive prefix of 128-key chunk counts) and the first
     // chunk that showed a key below t (INT_MAX while none has)
@@ -354,10 +364,19 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         if (tid == 0) {
             s_t = 0;
             s_nused = 0;
+            s_vin = 0;
+            s_exit = 0;
+            unsigned long long T = ~0ull;
+            if (a.stop_c && nl.last) {
+                const int g = a.gid ? a.gid[v] : 0;
+                T = a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g];
+            }
+            s_T = T;
         }
         __syncthreads();
         const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
         const int deg = (int)(e - b);
+        const bool can_stop = s_T != ~0ull;
         // t starts at max k[w,i-1] over alive neighbours (Prop. 3.1)
         int myk = 0;
         for (int64_t k = b + tid; k < e; k += blockDim.x) {
@@ -373,6 +392,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             if (slot >= 0) {
                 used[s_nused++] = (uint16_t)slot;
                 s_hist[rv] += 1;
+                s_vin = 1;
             }
         }
         __syncthreads();
@@ -416,7 +436,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         const int step = kKeysPerLane * G;
         int li = gid;  // neighbour index of this group's current list
         int pos = 0;
-        bool any = true;
+        bool any = true, stopped = false;
         while (any) {
             const int t = *(volatile int*)&s_t;
             if (flat) {
@@ -525,6 +545,19 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
                 const uint32_t over = __ballot_sync(kFull, S > nl.M);
                 const int pmax = over ? 31 - __clz(over) : -1;
+                if (can_stop) {
+                    // Def. 4.1 on the keys inserted so far plus v itself: a subset
+                    // of N(v;h) led by v, so by Prop. 4.2 at most the final estimate
+                    const int Sp = S + ((!s_vin && rv >= lane) ? 1 : 0);
+                    const uint32_t fits = __ballot_sync(kFull, Sp <= nl.M);
+                    const int k = fits ? __ffs(fits) - 1 : 32;
+                    const int Sk = __shfl_sync(kFull, Sp, k & 31);
+                    const unsigned long long part = estimate_of(k < 32 ? Sk : 0, k, rv, nl.M);
+                    if (lane == 0 && part > s_T) {
+                        s_exit = 1;
+                        s_part = part;
+                    }
+                }
                 if (lane == 0) {
                     const int told = s_t;
                     s_t = max(told, pmax + 1);
@@ -533,6 +566,10 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
             }
             __syncthreads();
+            if (s_exit && any) {  // (with every list read, finish: the exact value is kept)
+                stopped = true;
+                break;
+            }
             if (s_compact) {
                 // drop keys below t: empty their slots, re-insert the rest
                 const int tc = s_t, nu = min(s_nused, hcap);
@@ -556,6 +593,19 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
                 __syncthreads();
             }
+        }
+        if (stopped) {
+            // d(v) > T: v stays stale, its lower bound raised to the partial estimate
+            const int nu = min(s_nused, hcap);
+            for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
+            if (tid == 0) {
+                a.lb[v] = s_part;
+                a.fresh[v] = 0;
+                atomicAdd(a.updates, 1ull);
+                my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
+            }
+            __syncthreads();
+            continue;
         }
         const int kappa = s_t;
         const int nu = min(s_nused, hcap);
@@ -727,7 +777,7 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
                  int64_t count_static, int track, cudaStream_t s, int round_mode, int skip_last) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
-    LevelArgs a;
+    LevelArgs a{};
     a.rowptr = g.rowptr;
     a.col = g.col;
     a.alive = g.alive;
@@ -752,6 +802,12 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.heavy = g.listH;
     a.err = &g.state->err;
     a.updates = &g.state->updates;
+    const bool stop = round_mode == 2;
+    a.stop_c = stop ? g.pc : nullptr;
+    a.stop_mu = stop ? g.pmu : nullptr;
+    a.gid = g.gid;
+    a.lb = g.lb64;
+    a.fresh = g.fresh;
     int* rc = g.state->rc;
     if (round_mode == 1) {
         a.n_changed = rc + kRcC + level;
