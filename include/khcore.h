@@ -141,6 +141,16 @@ int kh_core_sampled(kh_graph *g, uint64_t *core, uint32_t flags);
  * Host pointers only. */
 int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updates);
 
+/* Work statistics of the last kh_core_* call (no counterpart in the paper).
+ * refreshed[i] / changed[i] (host int64[KH_MAX_H + 1], indexed by level i,
+ * each may be NULL): level-i lists recomputed by the rounds' refresh passes
+ * of kh_core_sampled, and how many of them came out different in size or
+ * level; *stopped (may be NULL): lazy refines that ended early because the
+ * partial ball or partial estimate already exceeded the round's threshold.
+ * KH_EINVAL before any peeling. */
+#define KH_MAX_H 16
+int kh_peel_stats(kh_graph *g, int64_t *refreshed, int64_t *changed, int64_t *stopped);
+
 /* Profiling of kernel classes (no counterpart in the paper; measurement aid).
  * kh_prof_enable(g, 1) resets the counters and brackets every later launch of
  * each kernel class with CUDA events on the context stream (peeling rounds

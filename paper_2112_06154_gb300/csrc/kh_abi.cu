@@ -149,6 +149,7 @@ int ensure_lists(Graph& g) {
     if (!g.lsz) g.lvl_alloc = g.hmax;
     if ((rc = dalloc(g.ctx, &g.lsz, (size_t)g.lvl_alloc * g.n, "list sizes"))) return rc;
     if ((rc = dalloc(g.ctx, &g.lk, (size_t)g.lvl_alloc * g.n, "list levels"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.rho, (size_t)g.n, "list change ranks"))) return rc;
     if (!g.ranks_valid) {
         launch_ranks(g, g.ctx->stream);
         g.ranks_valid = true;
@@ -208,6 +209,7 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.gbitmaps);
     dfree(&g.listH);
     dfree(&g.fresh);
+    dfree(&g.rho);
     dfree(&g.deadbm);
     dfree(&g.gid);
     dfree(&g.vtx_off);
@@ -660,6 +662,18 @@ int kh_peel_info(kh_graph* G, int32_t* round_of, int64_t* rounds, int64_t* updat
         cudaSetDevice(g.ctx->device);
         return kh::copy_out(g, round_of, g.round_of, sizeof(int32_t) * (size_t)g.n, 0);
     }
+    return KH_OK;
+}
+
+int kh_peel_stats(kh_graph* G, int64_t* refreshed, int64_t* changed, int64_t* stopped) {
+    if (!G) return KH_EINVAL;
+    Graph& g = G->g;
+    if (!g.have_rounds) return kh::set_error(g.ctx, KH_EINVAL, "no peeling has run on this graph");
+    for (int i = 0; i <= kh::kMaxH; ++i) {
+        if (refreshed) refreshed[i] = g.last_lvl_work[i];
+        if (changed) changed[i] = g.last_lvl_changed[i];
+    }
+    if (stopped) *stopped = g.last_stopped;
     return KH_OK;
 }
 

@@ -116,6 +116,7 @@ struct BfsArgs {
     const unsigned long long* stop_mu;
     unsigned long long* lb;
     uint8_t* fresh;
+    unsigned long long* stopped;  // early-stop count
 };
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 // v stays stale: its upper bound is kept, its lower bound raised
                 a.lb[v] = (unsigned long long)s_count;
                 a.fresh[v] = 0;
+                atomicAdd(a.stopped, 1ull);
             } else {
                 a.deg[v] = s_count;
             }
@@ -533,6 +535,7 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.stop_mu = stop ? g.pmu : nullptr;
     a.lb = g.lb64;
     a.fresh = g.fresh;
+    a.stopped = &g.state->stopped;
     if (!round_ctr) {
         e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");

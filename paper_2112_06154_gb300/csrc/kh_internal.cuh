@@ -81,6 +81,11 @@ struct DevState {
     unsigned long long minU;     // min of the upper bounds d over alive nodes
     int rc[kRcCount];            // per-round counters (kRc*)
     int done;                    // blocks of the round's final kernel that finished
+    // peel work statistics: list recomputations and changes per level in the
+    // rounds' refresh passes, refines stopped early
+    unsigned long long lvl_work[kMaxH + 1];
+    unsigned long long lvl_changed[kMaxH + 1];
+    unsigned long long stopped;
 };
 
 struct Graph;
@@ -113,6 +118,8 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
                  int skip_last = -1);
 // alive neighbours of the nodes in list1 and list2 (may be nullptr) join the
 // work list listW (count *out_count), deduplicated by stamp phase
+// A(list1) and the part of A(list2) whose level `phase` can have changed
+// (rank filter on rho) join the work list.
 void launch_mark_neighbours(Graph& g, const int* list1, const int* cnt1, const int* list2,
                             const int* cnt2, int phase, int* out_count, cudaStream_t s);
 // sampled mode: mark the nodes of `list` (nullptr: all) stale at the last
@@ -189,12 +196,18 @@ struct Graph {
     // current alive set; otherwise d[v] is an upper bound (d never grows as
     // nodes leave) and lb64[v] (exact mode) a lower bound
     uint8_t *fresh;
+    // rho[v]: highest rank among the elements that left or entered v's list in
+    // the level just recomputed (-1: none); filters the next level's refresh
+    int8_t *rho;
     uint32_t *deadbm;       // bitmap of removed nodes (n bits), seeds BFS visited sets
     int32_t *degX;          // alive degree (exact mode)
     unsigned long long *lb64;
     // last peel statistics
     int64_t last_rounds;
     int64_t last_updates;
+    int64_t last_lvl_work[kMaxH + 1];
+    int64_t last_lvl_changed[kMaxH + 1];
+    int64_t last_stopped;
     bool have_rounds;
     // profiling: CUDA events around every launch of a kernel class
     bool prof_on;

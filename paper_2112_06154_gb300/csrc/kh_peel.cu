@@ -557,6 +557,11 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     }
     g.last_rounds = hs.round;
     g.last_updates = (int64_t)hs.updates;
+    for (int i = 0; i <= kMaxH; ++i) {
+        g.last_lvl_work[i] = (int64_t)hs.lvl_work[i];
+        g.last_lvl_changed[i] = (int64_t)hs.lvl_changed[i];
+    }
+    g.last_stopped = (int64_t)hs.stopped;
     g.have_rounds = true;
     const size_t bytes = (size_t)g.n * (sampled ? sizeof(unsigned long long) : sizeof(int32_t));
     const void* src = sampled ? (const void*)g.core64 : (const void*)g.core32;

@@ -72,6 +72,11 @@ struct LevelArgs {
     const int32_t* gid;
     unsigned long long* lb;
     uint8_t* fresh;
+    // work statistics (indexed by level) and early-stop count
+    unsigned long long* lvl_work;
+    unsigned long long* lvl_changed;
+    unsigned long long* stopped;
+    int8_t* rho;  // tracked passes: top rank of each changed list's changes
 };
 
 constexpr int kL1Heavy = 512;
@@ -127,10 +132,33 @@ __device__ __forceinline__ void record_change(const LevelArgs& a, const NodeLeve
     const int old_k = nl.lk_out[v];
     nl.lsz_out[v] = S;
     nl.lk_out[v] = (uint8_t)kappa;
+    if (a.track) atomicAdd(a.lvl_work + nl.lvl, 1ull);
     if (a.track && (old_s != S || old_k != kappa)) {
+        atomicAdd(a.lvl_changed + nl.lvl, 1ull);
         const int p = atomicAdd(a.n_changed, 1);
         if (p < a.n) a.changed[p] = v;
     }
+}
+
+// rho of a tracked list about to be rewritten with (S, kappa): -2 when it is
+// unchanged (same size and level imply the same members, as the level never
+// rises and a list only gains members below its old level), else the highest
+// rank among the members that left and, if the level fell, old level - 1 (the
+// members that entered rank below the old level).  At level 1 the members that
+// leave are exactly the removed ones.  Warp-wide; every lane gets the result.
+__device__ __forceinline__ int level1_rho_warp(const LevelArgs& a, const NodeLevel& nl, int v,
+                                               int S, int kappa, int lane) {
+    const int old_s = nl.lsz_out[v], old_k = nl.lk_out[v];
+    if (old_s == S && old_k == kappa) return -2;
+    int r = kappa != old_k ? old_k - 1 : -1;
+    const uint32_t* old = nl.keys_out + (size_t)v * (size_t)a.cap;
+    const int m = min(old_s, (int)a.cap);
+    for (int p = lane; p < m; p += 32) {
+        const uint32_t key = old[p];
+        if (a.alive[key & kIdMask] != 1) r = max(r, (int)(key >> kIdBits));
+    }
+    for (int off = 16; off > 0; off >>= 1) r = max(r, __shfl_xor_sync(kFull, r, off));
+    return r;
 }
 
 // Bytes a node's level-1 computation must move: row offsets, the row, the
@@ -189,6 +217,11 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
                 atomicAdd(a.updates, 1ull);
             }
             continue;
+        }
+        if (a.track) {
+            // rho: the old list is read before it is overwritten
+            const int r = level1_rho_warp(a, nl, v, Skap, kappa, lane);
+            if (lane == 0 && r > -2) a.rho[v] = (int8_t)r;
         }
         // members grouped by rank, highest first: rank j starts at S_{j+1}
         const int above = __shfl_down_sync(kFull, S, 1);
@@ -269,6 +302,12 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
                 atomicAdd(a.bytes, level1_bytes(e - b, Skap, 1));
             }
         } else {
+            if (a.track && tid < 32) {
+                // rho (one warp); the old list is read before it is overwritten
+                const int r = level1_rho_warp(a, nl, v, Skap, kappa, lane);
+                if (lane == 0 && r > -2) a.rho[v] = (int8_t)r;
+            }
+            __syncthreads();
             uint32_t* out = nl.keys_out + (size_t)v * (size_t)a.cap;
             for (int64_t k = b + tid; k < e; k += blockDim.x) {
                 const int32_t u = a.col[k];
@@ -310,6 +349,20 @@ __device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, i
     return -1;
 }
 
+// Whether `key` is in the shared hash set (linear probing, no deletions
+// between rebuilds).
+__device__ __forceinline__ bool set_contains(const uint32_t* tab, int lg, uint32_t key) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t s = ((key & kIdMask) * 0x9E3779B1u) >> (32 - lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t x = tab[s];
+        if (x == key) return true;
+        if (x == kEmpty) return false;
+        s = (s + 1u) & mask;
+    }
+    return false;
+}
+
 // Keys one thread loads per step (one 16-byte vector); a warp's chunk.
 constexpr int kKeysPerLane = 4;
 constexpr int kChunkKeys = 32 * kKeysPerLane;
@@ -332,6 +385,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     __shared__ int s_hist[32];
     __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
     __shared__ int s_vin, s_exit;                // own key in the table; early stop taken
+    __shared__ int s_rho;
     __shared__ unsigned long long s_T, s_part;  // early-stop threshold; partial estimate
     // flat mode (degree <= kFlatMax): per neighbour list its node, size, first
     // chunk index (exclusive prefix of 128-key chunk counts) and the first
@@ -602,6 +656,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 a.lb[v] = s_part;
                 a.fresh[v] = 0;
                 atomicAdd(a.updates, 1ull);
+                atomicAdd(a.stopped, 1ull);
                 my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
             }
             __syncthreads();
@@ -622,6 +677,26 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             }
             for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
         } else {
+            if (a.track) {
+                // rho (see level1_rho_warp): an old member left iff its key is
+                // not in the new union, where every key of rank >= kappa is kept
+                const int old_s = nl.lsz_out[v], old_k = nl.lk_out[v];
+                if (old_s != S || old_k != kappa) {
+                    if (tid == 0) s_rho = kappa != old_k ? old_k - 1 : -1;
+                    __syncthreads();
+                    const uint32_t* old = nl.keys_out + (size_t)v * (size_t)a.cap;
+                    const int m = min(old_s, (int)a.cap);
+                    int r = -1;
+                    for (int p = tid; p < m; p += blockDim.x) {
+                        const uint32_t key = old[p];
+                        if (!set_contains(tab, lg, key)) r = max(r, (int)(key >> kIdBits));
+                    }
+                    for (int off = 16; off > 0; off >>= 1) r = max(r, __shfl_xor_sync(kFull, r, off));
+                    if (lane == 0 && r >= 0) atomicMax(&s_rho, r);
+                    __syncthreads();  // the old list is read before it is overwritten
+                    if (tid == 0) a.rho[v] = (int8_t)s_rho;
+                }
+            }
             // write members grouped by rank, highest first, emptying the table
             if (tid < 32) {
                 int above = 0;
@@ -652,14 +727,36 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
-// Alive neighbours of the listed nodes (two lists, the second optional) join
-// the work list once per stamp (round, phase).  One CTA per listed node.
+// Rank filter for the neighbours of changed lists.  Level i of u is the
+// rank filter (Prop. 3.1) of the union of its neighbours' level i-1 lists at
+// k[u,i]; if every change of a neighbour's list (members that left, or members
+// that entered below its old level) ranks below k[u,i] - 1, the counts S_j for
+// j >= k[u,i] - 1, the level and the members are all unchanged.  The test needs
+// k[u,i] for the current node set: intermediate levels always have it, a last
+// level only while u is fresh.
+struct MarkFilter {
+    const int8_t* rho;    // nullptr: no filter
+    const uint8_t* lk;    // k[u, phase]
+    const uint8_t* hv;    // per-node h (batches) or nullptr
+    int h;
+    const uint8_t* fresh;
+};
+
+__device__ __forceinline__ bool level_may_change(const MarkFilter& f, int u, int rw, int level) {
+    const int hu = f.hv ? (int)f.hv[u] : f.h;
+    const bool known = level < hu || (level == hu && f.fresh[u]);
+    return !known || rw >= (int)f.lk[u] - 1;
+}
+
+// Alive neighbours of the listed nodes (two lists, the second optional and
+// rank-filtered) join the work list once per stamp (round, phase).  One CTA
+// per listed node.
 __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                             const int32_t* __restrict__ list1, const int* __restrict__ nlist1,
                             const int32_t* __restrict__ list2, const int* __restrict__ nlist2,
                             int32_t* __restrict__ wl, int* nwl, const DevState* __restrict__ st,
-                            int phase, int64_t cap, unsigned long long* bytes) {
+                            int phase, int64_t cap, unsigned long long* bytes, MarkFilter f) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n1 = *nlist1;
     const int nin = n1 + (list2 ? *nlist2 : 0);
@@ -667,6 +764,8 @@ __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* _
     unsigned long long my_bytes = 0;
     for (int64_t i = blockIdx.x; i < nin; i += gridDim.x) {
         const int w = i < n1 ? list1[i] : list2[i - n1];
+        const bool filt = f.rho != nullptr && i >= n1;
+        const int rw = filt ? (int)f.rho[w] : 0;
         const int64_t b = rowptr[w], e = rowptr[w + 1];
         if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
         for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
@@ -675,7 +774,8 @@ __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* _
             int32_t u = 0;
             if (k < e) {
                 u = col[k];
-                if (alive[u] == 1 && *(volatile int32_t*)(seen + u) != stamp)
+                if (alive[u] == 1 && (!filt || level_may_change(f, u, rw, phase)) &&
+                    *(volatile int32_t*)(seen + u) != stamp)
                     isnew = atomicExch(seen + u, stamp) != stamp;
             }
             const uint32_t m = __ballot_sync(kFull, isnew);
@@ -808,6 +908,10 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.gid = g.gid;
     a.lb = g.lb64;
     a.fresh = g.fresh;
+    a.rho = g.rho;
+    a.lvl_work = g.state->lvl_work;
+    a.lvl_changed = g.state->lvl_changed;
+    a.stopped = &g.state->stopped;
     int* rc = g.state->rc;
     if (round_mode == 1) {
         a.n_changed = rc + kRcC + level;
@@ -875,9 +979,17 @@ void launch_mark_neighbours(Graph& g, const int* list1, const int* cnt1, const i
                             const int* cnt2, int phase, int* out_count, cudaStream_t s) {
     const int grid = g.ctx->sm_count * 8;
     prof_begin(g, kProfFrontier, s);
+    MarkFilter f{};
+    if (list2) {
+        f.rho = g.rho;
+        f.lk = g.lk + (size_t)(phase - 1) * (size_t)g.n;
+        f.hv = g.hv;
+        f.h = g.h;
+        f.fresh = g.fresh;
+    }
     k_mark_nbrs<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, list1, cnt1, list2, cnt2,
                                      g.listW, out_count, g.state, phase, g.n,
-                                     &g.state->bytes[kProfFrontier]);
+                                     &g.state->bytes[kProfFrontier], f);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

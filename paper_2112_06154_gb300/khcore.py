@@ -60,6 +60,7 @@ SIGNATURES = [
     ("kh_prof_enable", ctypes.c_int, [_P, ctypes.c_int32]),
     ("kh_prof_read", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _I64P,
                                     ctypes.POINTER(ctypes.c_double)]),
+    ("kh_peel_stats", ctypes.c_int, [_P, _P, _P, _I64P]),
     ("kh_prof_trace", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -271,6 +272,18 @@ def kh_peel_info(g: Graph, want_rounds: bool = True):
     p, _ = _ptr(ro)
     _check(load().kh_peel_info(g.handle, p, ctypes.byref(rounds), ctypes.byref(updates)), g.ctx)
     return ro, int(rounds.value), int(updates.value)
+
+
+KH_MAX_H = 16
+
+
+def kh_peel_stats(g: Graph):
+    """(refreshed int64[KH_MAX_H+1], changed int64[KH_MAX_H+1], stopped) of the last peel."""
+    ref = np.zeros(KH_MAX_H + 1, np.int64)
+    chg = np.zeros(KH_MAX_H + 1, np.int64)
+    st = ctypes.c_int64()
+    _check(load().kh_peel_stats(g.handle, ref.ctypes.data, chg.ctypes.data, ctypes.byref(st)), g.ctx)
+    return ref, chg, int(st.value)
 
 
 def kh_sync(g: Graph):
