@@ -69,6 +69,11 @@ int ensure_work(Graph& g) {
     if ((rc = dalloc(g.ctx, &g.deadbm, ((n + 127) / 128) * 4, "deadbm"))) return rc;
     if ((rc = dalloc(g.ctx, &g.degX, n, "degX"))) return rc;
     if ((rc = dalloc(g.ctx, &g.lb64, n, "lb64"))) return rc;
+    if (!g.loss) {
+        if ((rc = dalloc(g.ctx, &g.loss, n, "loss"))) return rc;
+        KH_CUDA_TRY(g.ctx, cudaMemset(g.loss, 0, sizeof(int32_t) * (n ? n : 1)));
+    }
+    if ((rc = dalloc(g.ctx, &g.listL, n, "listL"))) return rc;
     const size_t ng = (size_t)(g.gid ? g.ngraphs : 1);
     if ((rc = dalloc(g.ctx, &g.pc, ng, "per-graph c"))) return rc;
     if ((rc = dalloc(g.ctx, &g.pmn, ng, "per-graph minimum"))) return rc;
@@ -210,6 +215,8 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.listH);
     dfree(&g.fresh);
     dfree(&g.rho);
+    dfree(&g.loss);
+    dfree(&g.listL);
     dfree(&g.deadbm);
     dfree(&g.gid);
     dfree(&g.vtx_off);

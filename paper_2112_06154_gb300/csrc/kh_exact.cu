@@ -117,13 +117,34 @@ struct BfsArgs {
     unsigned long long* lb;
     uint8_t* fresh;
     unsigned long long* stopped;  // early-stop count
+    // loss mode (nullptr: off): per-node loss counters and their list, the
+    // ball stamps of the round and where the round index lives
+    int32_t* loss;
+    int32_t* loss_list;
+    int* n_loss;
+    const int32_t* seen;
+    const int* round;
 };
+
+// Loss mode: u was first reached at the source's last hop.  Unless u is within
+// h-1 hops of the removed set (stamped by the ball hops and made stale), every
+// path of at most h edges from u avoids the removed nodes except at its end,
+// so u's h-ball loses exactly the removed nodes within h hops: count this one.
+__device__ __forceinline__ void loss_mark(const BfsArgs& a, int32_t u) {
+    if (a.alive[u] != 1) return;
+    if (a.seen[u] == (*a.round) * kPhaseStride) return;
+    if (atomicAdd(a.loss + u, 1) == 0) {
+        const int p = atomicAdd(a.n_loss, 1);
+        if (p < a.n) a.loss_list[p] = u;
+    }
+}
 
 // Visit neighbour u of a frontier vertex (all 32 lanes call this together;
 // `valid` false for lanes past the end of the row).
 template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
 __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
-                                      int* s_hist, bool valid, int32_t u, bool push, int lane,
+                                      int* s_hist, bool valid, int32_t u, bool push, bool last,
+                                      int lane,
                                       int& my, int32_t base) {
     bool isnew = false;
     // seeded: removed nodes already have their bit set, no alive lookup needed;
@@ -140,6 +161,7 @@ __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q
     if (isnew) {
         ++my;
         if (RANKS) atomicAdd(&s_hist[a.rank[u]], 1);
+        if (last && a.loss) loss_mark(a, u);
     }
     if (push) {
         const uint32_t nm = __ballot_sync(kFull, isnew);
@@ -170,7 +192,7 @@ __device__ __forceinline__ void fold_count(int& my, int* s_count, int lane) {
 template <bool RANKS, bool SEEDED, bool ALLALIVE = false>
 __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32_t* q, int* s_qtail,
                                            int* s_hist, int64_t b, int64_t e, int64_t first,
-                                           int64_t stride, bool push, int lane, int& my,
+                                           int64_t stride, bool push, bool last, int lane, int& my,
                                            int32_t base) {
     for (int64_t k0 = b + first; k0 < e; k0 += stride) {
         int32_t u[4];
@@ -183,7 +205,7 @@ __device__ __forceinline__ void expand_row(const BfsArgs& a, uint32_t* bm, int32
         }
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq)
-            visit<RANKS, SEEDED, ALLALIVE>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, lane, my,
+            visit<RANKS, SEEDED, ALLALIVE>(a, bm, q, s_qtail, s_hist, val[qq], u[qq], push, last, lane, my,
                                            base);
     }
 }
@@ -214,8 +236,9 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
         const int64_t idx = s_src;
         if (idx >= total) break;
         const int v = a.worklist ? a.worklist[idx] : (int)idx;
-        if (!ALLALIVE && a.alive[v] != 1) {
-            if (tid == 0) a.deg[v] = 0;
+        // loss mode starts from the round's removed nodes (alive == 2)
+        if (!ALLALIVE && (a.loss ? a.alive[v] == 0 : a.alive[v] != 1)) {
+            if (tid == 0 && !a.loss) a.deg[v] = 0;
             if (RANKS && tid < a.nj) a.cnt[(size_t)v * a.nj + tid] = 0;
             __syncthreads();
             continue;
@@ -256,6 +279,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             // vertices found at distance d+1 are queued if they will be expanded,
             // or, in global-bitmap mode, so the bitmap can be cleared by a walk
             const bool push = (d + 1 < hsrc) || !SMEM;
+            const bool last = d + 1 == hsrc;
             if (tid == 0) s_nheavy = 0;
             __syncthreads();
             const bool single = (fe - fs) == 1;
@@ -281,11 +305,11 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                     }
                 }
                 if (seeded)
-                    expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, lane, my,
+                    expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push, last, lane, my,
                                             base);
                 else
                     expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, 0, 128, push,
-                                                       lane, my, base);
+                                                       last, lane, my, base);
                 if (can_stop) fold_count(my, &s_count, lane);
             }
             __syncthreads();
@@ -304,10 +328,10 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 const int64_t b = a.rowptr[w], e = a.rowptr[w + 1];
                 if (seeded)
                     expand_row<RANKS, true>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
-                                            4 * blockDim.x, push, lane, my, base);
+                                            4 * blockDim.x, push, last, lane, my, base);
                 else
                     expand_row<RANKS, false, ALLALIVE>(a, bm, q, &s_qtail, s_hist, b, e, warp * 128,
-                                                       4 * blockDim.x, push, lane, my, base);
+                                                       4 * blockDim.x, push, last, lane, my, base);
             }
             __syncthreads();
             if (s_stop) break;  // d(v) > T: the rest of the ball is not needed
@@ -319,7 +343,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
         for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(kFull, my, off);
         if (lane == 0 && my) atomicAdd(&s_count, my);
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !a.loss) {
             if (s_stop) {
                 // v stays stale: its upper bound is kept, its lower bound raised
                 a.lb[v] = (unsigned long long)s_count;
@@ -353,15 +377,18 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
-// One hop of the ball around the removed set R in the OLD graph (alive != 0):
-// every newly reached vertex joins the next frontier (if more hops follow) and,
-// when it is still alive (alive == 1), the recompute work list.  One CTA per
-// frontier vertex, so a hub's row is spread over all of the CTA's warps.
+// One hop of the ball around the removed set R in the OLD graph (alive != 0),
+// for hops 1 .. h-1: every newly reached vertex is stamped, joins the next
+// frontier (if a further hop below h follows) and, when it is still alive
+// (alive == 1), the stale list.  Hop 1 also lowers the alive degrees of R's
+// neighbours (with h = 1 it stamps nothing).  Nodes exactly h hops from R are
+// handled by the loss BFS instead.  One CTA per frontier vertex, so a hub's row
+// is spread over all of the CTA's warps.
 __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                            const int32_t* __restrict__ fin, const int* __restrict__ nfin,
                            int32_t* __restrict__ fout, int* nfout, int32_t* __restrict__ wl, int* nwl,
-                           const DevState* __restrict__ st, int push_next, int64_t cap,
+                           const DevState* __restrict__ st, int h_all, int64_t cap,
                            unsigned long long* bytes, int32_t* __restrict__ degX,
                            const uint8_t* __restrict__ hv, int hop) {
     if (st->early) return;
@@ -378,16 +405,17 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
             bool isnew = false;
             int32_t u = 0;
             uint8_t au = 0;
+            int hu = h_all;
             if (k < e) {
                 u = col[k];
                 au = alive[u];
+                if (hv) hu = (int)hv[u];  // batches: the h of u's graph
                 // hop 1 scans each removed node's row once: alive neighbours lose a degree
                 if (degX && au == 1) atomicSub(degX + u, 1);
-                if (au != 0 && *(volatile int32_t*)(seen + u) != stamp)
+                if (au != 0 && hop < hu && *(volatile int32_t*)(seen + u) != stamp)
                     isnew = atomicExch(seen + u, stamp) != stamp;
             }
-            // batches: a node is expanded further only while hop < its graph's h
-            const bool to_f = isnew && (hv ? hop < (int)hv[u] : push_next != 0);
+            const bool to_f = isnew && hop + 1 < hu;
             const bool to_w = isnew && au == 1;
             uint32_t m1 = __ballot_sync(kFull, to_f);
             uint32_t m2 = __ballot_sync(kFull, to_w);
@@ -454,6 +482,31 @@ __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t*
     if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
+// The nodes the loss BFS reached keep their state: d (exact when fresh, an
+// upper bound when stale) and the stale lower bound both drop by the loss.
+// Each is one h-degree update (an incremental recomputation).
+__global__ void k_apply_loss(const int32_t* __restrict__ list, const int* __restrict__ nlist,
+                             int32_t* __restrict__ loss, int32_t* __restrict__ d,
+                             const uint8_t* __restrict__ fresh, unsigned long long* __restrict__ lb,
+                             DevState* __restrict__ st, int64_t cap) {
+    if (st->early) return;
+    const int cnt = (int)min((int64_t)*nlist, cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cnt > 0) {
+        atomicAdd(&st->updates, (unsigned long long)cnt);
+        atomicAdd(&st->bytes[kProfFrontier], 21ull * (unsigned long long)cnt);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int v = list[i];
+        const int l = loss[v];
+        loss[v] = 0;
+        d[v] -= l;
+        if (!fresh[v]) {
+            const unsigned long long x = lb[v];
+            lb[v] = x > (unsigned long long)l ? x - (unsigned long long)l : 0ull;
+        }
+    }
+}
+
 int pick_grid(int sm, int per_sm, int64_t work) {
     int64_t g = (int64_t)sm * per_sm;
     if (work < g) g = work;
@@ -478,7 +531,7 @@ void launch_validate(const Graph& g, int* d_err, cudaStream_t s) {
 
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
                 int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s, int* round_ctr,
-                bool early_stop) {
+                bool early_stop, bool loss) {
     if (g.n == 0) return KH_OK;
     if (!worklist && count_static == 0) return KH_OK;
     // batches index the visited bitmap inside the source's graph
@@ -530,7 +583,14 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.gid = g.gid;
     a.vtx_off = g.vtx_off;
     a.hv = g.hv;
-    const bool stop = early_stop && !cnt;
+    const bool stop = early_stop && !cnt && !loss;
+    if (loss) {
+        a.loss = g.loss;
+        a.loss_list = g.listL;
+        a.n_loss = &g.state->rc[kRcLossCount];
+        a.seen = g.seen;
+        a.round = &g.state->round;
+    }
     a.stop_c = stop ? g.pc : nullptr;
     a.stop_mu = stop ? g.pmu : nullptr;
     a.lb = g.lb64;
@@ -556,9 +616,18 @@ void launch_ball_hop(Graph& g, int hop, cudaStream_t s) {
     const int grid = g.ctx->sm_count * 8;
     prof_begin(g, kProfFrontier, s);
     k_ball_hop<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.seen, fin, nfin, fout, nfout,
-                                    g.listW, &g.state->rc[kRcW], g.state, hop < g.h ? 1 : 0, g.n,
+                                    g.listW, &g.state->rc[kRcW], g.state, g.h, g.n,
                                     &g.state->bytes[kProfFrontier], hop == 1 ? g.degX : nullptr,
                                     g.hv, hop);
+    count_launch(g, 1);
+    prof_end(g, kProfFrontier, s);
+}
+
+void launch_apply_loss(Graph& g, cudaStream_t s) {
+    const int grid = g.ctx->sm_count * 4;
+    prof_begin(g, kProfFrontier, s);
+    k_apply_loss<<<grid, 256, 0, s>>>(g.listL, &g.state->rc[kRcLossCount], g.loss, g.d32, g.fresh,
+                                      g.lb64, g.state, g.n);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

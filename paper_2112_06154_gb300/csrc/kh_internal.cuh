@@ -61,7 +61,9 @@ constexpr int kRcLevelHeavy = 20;  // + i: refresh level i heavy count
 constexpr int kRcW = 37;           // + i: work list of level i (0: exact affected nodes)
 constexpr int kRcF = 54;           // + hop: frontier written by that hop (exact)
 constexpr int kRcC = 71;           // + i: changed nodes at level i
-constexpr int kRcCount = 88;
+constexpr int kRcLossWork = 88;    // exact refresh: loss-BFS work counter
+constexpr int kRcLossCount = 89;   // exact refresh: nodes with a loss this round
+constexpr int kRcCount = 90;
 
 struct DevState {
     unsigned long long c;        // current core value (max of round minima)
@@ -98,9 +100,14 @@ void launch_validate(const Graph& g, int* d_err, cudaStream_t s);
 // early_stop (the peel's lazy refine): a source whose partial ball already
 // holds more than T = max(c, mu) of its graph stops and stays stale with that
 // count as its lower bound.
+// loss (the peel's exact refresh): sources are the removed nodes of the round;
+// every alive node first reached at the source's last hop and not within h-1
+// hops of the removed set (ball stamp) gains one in loss[] instead of a degree.
 int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count_static,
                 int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
-                int* round_ctr = nullptr, bool early_stop = false);
+                int* round_ctr = nullptr, bool early_stop = false, bool loss = false);
+// d and (stale nodes) lb drop by loss[] for the listed nodes; loss[] is cleared
+void launch_apply_loss(Graph& g, cudaStream_t s);
 // one hop of the removed set's ball in the old graph (exact refresh)
 void launch_ball_hop(Graph& g, int hop, cudaStream_t s);
 // exact mode: mark the nodes of `list` (nullptr: all) stale and set their
@@ -202,6 +209,10 @@ struct Graph {
     uint32_t *deadbm;       // bitmap of removed nodes (n bits), seeds BFS visited sets
     int32_t *degX;          // alive degree (exact mode)
     unsigned long long *lb64;
+    // exact refresh: loss[v] = removed nodes within h hops of a node exactly
+    // h hops from the removed set (zero between rounds), listed in listL
+    int32_t *loss;
+    int32_t *listL;
     // last peel statistics
     int64_t last_rounds;
     int64_t last_updates;

@@ -400,9 +400,16 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     prof_end(g, kProfPeel, s);
     if (!sampled) {
         // the ball of R in the old graph: alive degrees drop (hop 1), the
-        // nodes within h hops become stale with new lower bounds
-        for (int hop = 1; hop <= g.hmax; ++hop) launch_ball_hop(g, hop, s);
+        // nodes within h-1 hops become stale with new lower bounds ...
+        const int hops = g.hmax > 2 ? g.hmax - 1 : 1;
+        for (int hop = 1; hop <= hops; ++hop) launch_ball_hop(g, hop, s);
         launch_stale_exact(g, g.listW, &g.state->rc[kRcW], s);
+        // ... and the nodes exactly h hops away lose exactly the removed nodes
+        // within h hops: their values (and bounds) are decremented in place
+        rc = launch_hdeg(g, g.listR, &g.state->nR, 0, g.d32, nullptr, 0, 0, s,
+                         &g.state->rc[kRcLossWork], false, true);
+        if (rc) return rc;
+        launch_apply_loss(g, s);
     } else {
         int* rcs = g.state->rc;
         for (int i = 1; i <= g.hmax && rc == KH_OK; ++i) {
@@ -500,6 +507,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.seen, 0xff, sizeof(int32_t) * (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
+    if (!sampled) KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.loss, 0, sizeof(int32_t) * (size_t)g.n, s));
     DevState init;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&init, g.state, sizeof(init), cudaMemcpyDeviceToHost, s));
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
