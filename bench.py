@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
                                     "sampled3", "exact2"],
                    help="run one operation of the step once (a target for profilers) and exit")
-    p.add_argument("--workload", choices=["chung_lu", "batch", "serve"], default="chung_lu",
+    p.add_argument("--workload", choices=["chung_lu", "batch", "serve", "rmat"], default="chung_lu",
                    help="batch: 4096 preferential-attachment graphs, batched vs one graph per call; "
                         "serve: a Poisson request stream through the continuous-batching server")
     p.add_argument("--requests", type=int, default=300)
@@ -404,6 +404,53 @@ def run_op(args):
     ctx.close()
 
 
+def run_rmat(args):
+    """R-MAT scale 22 (a=.57, b=c=.19, 16 edges per node generated, symmetrised,
+    deduplicated): exact h-degrees at h=2, adaptive estimates and sampled
+    (k,h)-cores at h=2,3,4, each timed once after a warm-up load."""
+    import torch
+    from paper_2112_06154_gb300 import graphgen as gg
+    from paper_2112_06154_gb300 import khcore as K
+    K.load()
+    t0 = time.perf_counter()
+    rowptr, col = gg.rmat(22, 16, 0.57, 0.19, 0.19, 1003)
+    stats = gg.graph_stats(rowptr, col)
+    gen_s = time.perf_counter() - t0
+    ctx = K.kh_ctx_create(0)
+    G = K.kh_graph_load_csr(ctx, rowptr, col)
+    K.kh_set_sampling(G, seed=1)
+    out = {"workload": "rmat_scale22", "impl": "ours", "graph": stats, "M": K.kh_get_M(G),
+           "gen_s": gen_s, "unit": "s", "higher_is_better": False}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    K.kh_set_h(G, 2)
+    K.kh_prof_enable(G, True)
+    _, out["hdeg_h2_s"] = timed(lambda: K.kh_hdegree_exact(G))
+    ms, _, b = K.kh_prof_read(G, K.KH_PROF_BFS)
+    K.kh_prof_enable(G, False)
+    out["hdeg_h2_alg_GBps"] = b / 1e6 / ms if ms > 0 else None
+    for h in (2, 3, 4):
+        K.kh_set_h(G, h)
+        _, out[f"estimate_h{h}_s"] = timed(lambda: K.kh_estimate(G))
+    for h in (2, 3, 4):
+        K.kh_set_h(G, h)
+        core, secs = timed(lambda: K.kh_core_sampled(G))
+        _, rounds, updates = K.kh_peel_info(G, False)
+        out[f"core_sampled_h{h}"] = {"s": secs, "rounds": rounds, "updates": updates,
+                                     "max_core": int(core.max())}
+    free, total = torch.cuda.mem_get_info()
+    out["device_gib_used"] = (total - free) / 2**30
+    print(json.dumps(out), flush=True)
+    G.close()
+    ctx.close()
+
+
 def run_batch(args):
     """Batched workload: many preferential-attachment graphs (n log-uniform in
     [100, 20000], m uniform in {3..8}, h uniform in {2,3,4}, per-graph M).
@@ -557,6 +604,8 @@ def main():
         run_serve(args)
     elif args.workload == "batch" and args.impl == "ours":
         run_batch(args)
+    elif args.workload == "rmat" and args.impl == "ours":
+        run_rmat(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
