@@ -70,6 +70,8 @@ def _load():
     lib.kho_hdegree_some.restype = ctypes.c_int
     lib.kho_estimate_def_some.argtypes = [i64, P, P, P, P, i32, i64, P, i64, P, P, P]
     lib.kho_estimate_def_some.restype = ctypes.c_int
+    lib.kho_dense_curve.argtypes = [i64, P, P, P, i32, i64, i32, P, i32, P, P]
+    lib.kho_dense_curve.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -218,3 +220,16 @@ def estimate_def_some(rowptr, col, r, h: int, M: int, vertices, alive=None):
                                          _p(vs), vs.size, _p(est), _p(k), _p(bs)),
            "estimate_def_some")
     return est[:vs.size], k[:vs.size], bs[:vs.size]
+
+
+def dense_curve(rowptr, col, r, h: int, M: int, exact: bool, round_of, rounds: int):
+    """EstDense (Alg. 7): (sum uint64[rounds], size int64[rounds]) with
+    sum[q] = sum of d(v; X_q) over X_q = {v : round_of[v] >= q}."""
+    rowptr, col, n = _graph(rowptr, col)
+    r = np.ascontiguousarray(r, dtype=np.uint8)
+    ro = np.ascontiguousarray(round_of, dtype=np.int32)
+    total = np.zeros(max(rounds, 1), dtype=np.uint64)
+    size = np.zeros(max(rounds, 1), dtype=np.int64)
+    _check(_load().kho_dense_curve(n, _p(rowptr), _p(col), _p(r), h, max(M, 1), 1 if exact else 0,
+                                   _p(ro), rounds, _p(total), _p(size)), "dense_curve")
+    return total[:rounds], size[:rounds]

@@ -22,6 +22,8 @@
  *                         level (Prop. 3.1), then Estimate (Alg. 1).
  *   kho_core_exact        ExactCore (Sec. 2): peel by smallest deg_h.
  *   kho_core_sampled      Core (Alg. 4) with naive Update (Alg. 3).
+ *   kho_dense_curve       EstDense (Alg. 7, Sec. 6): along a removal order, the
+ *                         sum of d(v; X) over each candidate set X.
  *
  * Peeling schedule.  Both peels support two schedules that must give the same
  * core map because d(v; X) never grows when X shrinks (exact: N shrinks; sampled:
@@ -838,5 +840,70 @@ int kho_estimate_def_some(int64_t n, const int64_t *rowptr, const int32_t *col,
     free(buf);
     free(dist);
     free(x);
+    return KHO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* EstDense (Alg. 7)                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Alg. 7 deletes the nodes in the order Core produced and, for every set X it
+ * passes through, estimates the h-density |E_h(X)| / |X| from the identity
+ * 2 |E_h(X)| = sum_{v in X} deg_h(v; X), with deg_h replaced by the estimate
+ * of Alg. 1 in the sampled form.  The candidates here are the sets at the
+ * boundaries of a removal order given by rounds: X_r = {v : round_of[v] >= r}
+ * (one node per round gives the paper's n candidates).  For r in [0, rounds):
+ * size[r] = |X_r| and sum[r] = sum over v in X_r of d(v; X_r), where d is
+ * deg_h (exact != 0) or Def. 4.1 on the rank list of N(v; h, X_r), v first. */
+int kho_dense_curve(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *r,
+                    int32_t h, int64_t M, int32_t exact, const int32_t *round_of, int32_t rounds,
+                    uint64_t *sum, int64_t *size)
+{
+    if (rounds < 0 || (!exact && M < 1))
+        return KHO_EINVAL;
+    for (int64_t v = 0; v < n; v++)
+        if (round_of[v] < 0 || round_of[v] >= rounds)
+            return KHO_EINVAL;
+    int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    uint8_t *x = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    uint8_t *alive = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!buf || !dist || !x || !alive) {
+        free(buf);
+        free(dist);
+        free(x);
+        free(alive);
+        return KHO_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; i++)
+        dist[i] = -1;
+    for (int32_t q = 0; q < rounds; q++) {
+        int64_t cnt = 0;
+        uint64_t s = 0;
+        for (int64_t v = 0; v < n; v++) {
+            alive[v] = round_of[v] >= q ? 1 : 0;
+            cnt += alive[v];
+        }
+        for (int64_t v = 0; v < n; v++) {
+            if (!alive[v])
+                continue;
+            int64_t d = kho_hball(n, rowptr, col, alive, v, h, buf, dist);
+            if (exact) {
+                s += d > 0 ? (uint64_t)(d - 1) : 0;
+            } else if (d > 0) {
+                uint8_t k = 0;
+                int32_t bs = 0;
+                for (int64_t j = 0; j < d; j++)
+                    x[j] = r[buf[j]];
+                s += def41(x, d, M, &k, &bs);
+            }
+        }
+        sum[q] = s;
+        size[q] = cnt;
+    }
+    free(buf);
+    free(dist);
+    free(x);
+    free(alive);
     return KHO_OK;
 }

@@ -360,3 +360,74 @@ def test_round_of_is_consistent():
     for k in range(steps):
         vals = np.unique(core[rnd == k])
         assert vals.size == 1
+
+
+# --------------------------------------------------------------- EstDense (Alg. 7)
+
+def brute_pairs_within_h(rowptr, col, h, alive):
+    """|E_h(X)|: unordered pairs of X joined by a path of at most h edges in G[X]."""
+    D = induced_dist(rowptr, col, alive)
+    idx = np.nonzero(alive)[0]
+    sub = D[np.ix_(idx, idx)]
+    return int(((sub <= h) & (sub > 0)).sum() // 2)
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_dense_curve_exact_counts_pairs(h):
+    # the identity behind Alg. 7: sum_v deg_h(v; X) = 2 |E_h(X)|, on every candidate set
+    rowptr, col = gg.erdos_renyi(40, 70, 31 + h)
+    n = rowptr.size - 1
+    r = O.ranks(n, 3)
+    _, rnd, _ = O.core_exact(rowptr, col, h)
+    rounds = int(rnd.max()) + 1
+    total, size = O.dense_curve(rowptr, col, r, h, 8, True, rnd, rounds)
+    for q in range(rounds):
+        alive = rnd >= q
+        assert size[q] == alive.sum()
+        assert total[q] == 2 * brute_pairs_within_h(rowptr, col, h, alive)
+
+
+def test_dense_curve_closed_forms():
+    # K_n: every pair at distance 1, sum = n (n - 1); star with L leaves at h = 2:
+    # every node reaches all others, sum = (L + 1) L
+    for n in (2, 5, 9):
+        rowptr, col = gg.complete(n)
+        total, size = O.dense_curve(rowptr, col, O.ranks(n, 1), 1, 4, True, np.zeros(n, np.int32), 1)
+        assert total[0] == n * (n - 1) and size[0] == n
+    for L in (3, 7):
+        rowptr, col = gg.star(L)
+        n = L + 1
+        total, _ = O.dense_curve(rowptr, col, O.ranks(n, 1), 2, 4, True, np.zeros(n, np.int32), 1)
+        assert total[0] == (L + 1) * L
+
+
+def test_dense_curve_sampled_is_exact_when_M_ge_n():
+    rowptr, col = gg.erdos_renyi(60, 150, 41)
+    n = rowptr.size - 1
+    r = O.ranks(n, 9)
+    _, rnd, _ = O.core_exact(rowptr, col, 2)
+    rounds = int(rnd.max()) + 1
+    ex, _ = O.dense_curve(rowptr, col, r, 2, n, True, rnd, rounds)
+    sa, _ = O.dense_curve(rowptr, col, r, 2, n, False, rnd, rounds)
+    assert np.array_equal(ex, sa)
+
+
+def test_dense_curve_sampled_is_sum_of_definition_estimates():
+    # sampled form: Def. 4.1 per node on X_q, summed; a schedule of one node per
+    # round gives the paper's n candidates
+    rowptr, col = gg.barabasi_albert(50, 3, 5)
+    n = rowptr.size - 1
+    r = O.ranks(n, 11)
+    order = np.random.default_rng(2).permutation(n).astype(np.int32)
+    total, size = O.dense_curve(rowptr, col, r, 2, 6, False, order, n)
+    for q in (0, 7, 31, n - 1):
+        alive = order >= q
+        est, _, _ = O.estimate_def(rowptr, col, r, 2, 6, alive=alive)
+        assert total[q] == int(est[alive].astype(np.uint64).sum())
+        assert size[q] == n - q
+
+
+def test_dense_curve_rejects_bad_schedules():
+    rowptr, col = gg.erdos_renyi(10, 12, 1)
+    with pytest.raises(Exception):
+        O.dense_curve(rowptr, col, O.ranks(10, 1), 2, 4, True, np.full(10, 3, np.int32), 2)
