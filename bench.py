@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
                                     "sampled3", "exact2"],
                    help="run one operation of the step once (a target for profilers) and exit")
-    p.add_argument("--workload", choices=["chung_lu", "batch", "serve", "rmat"], default="chung_lu",
+    p.add_argument("--workload", choices=["chung_lu", "batch", "serve", "rmat", "dense"],
+                   default="chung_lu",
                    help="batch: 4096 preferential-attachment graphs, batched vs one graph per call; "
                         "serve: a Poisson request stream through the continuous-batching server")
     p.add_argument("--requests", type=int, default=300)
@@ -451,6 +452,46 @@ def run_rmat(args):
     ctx.close()
 
 
+def run_dense(args):
+    """EstDense (Alg. 7) on the Chung-Lu n=200k graph: the removal order of a
+    sampled (k,h)-core (rank seed 1) replayed with fresh ranks (seed 2), h = 2
+    and 3, and the exact form along the exact (k,2)-core.  Each call is timed
+    once after a warm-up call."""
+    import torch
+    from paper_2112_06154_gb300 import khcore as K
+    K.load()
+    rowptr, col = make_graph()
+    ctx = K.kh_ctx_create(0)
+    G = K.kh_graph_load_csr(ctx, rowptr, col)
+    out = {"workload": "estdense_chung_lu_n200k", "impl": "ours", "unit": "s",
+           "higher_is_better": False}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    for h, exact in ((2, False), (3, False), (2, True)):
+        K.kh_set_h(G, h)
+        K.kh_set_sampling(G, seed=1)
+        (_, secs_core) = timed(lambda: K.kh_core_exact(G) if exact else K.kh_core_sampled(G))
+        order, rounds, _ = K.kh_peel_info(G, True)
+        if not exact:
+            K.kh_set_sampling(G, seed=2)
+        (total, size, best), secs = timed(lambda: K.kh_dense(G, exact, order, rounds))
+        _, _, updates = K.kh_peel_info(G, False)
+        key = f"{'exact' if exact else 'sampled'}_h{h}"
+        out[key] = {"dense_s": secs, "core_s": secs_core, "rounds": rounds, "updates": updates,
+                    "best_round": best, "best_size": int(size[best]),
+                    "best_density": float(total[best]) / (2.0 * float(size[best]))}
+    print(json.dumps(out), flush=True)
+    G.close()
+    ctx.close()
+
+
 def run_batch(args):
     """Batched workload: many preferential-attachment graphs (n log-uniform in
     [100, 20000], m uniform in {3..8}, h uniform in {2,3,4}, per-graph M).
@@ -606,6 +647,8 @@ def main():
         run_batch(args)
     elif args.workload == "rmat" and args.impl == "ours":
         run_rmat(args)
+    elif args.workload == "dense" and args.impl == "ours":
+        run_dense(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

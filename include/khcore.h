@@ -141,6 +141,22 @@ int kh_core_sampled(kh_graph *g, uint64_t *core, uint32_t flags);
  * Host pointers only. */
 int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updates);
 
+/* EstDense (Alg. 7, Sec. 6): replays a removal order and, at the start of
+ * every round q, sums d(v; X_q) over X_q = {v : round_of[v] >= q}, where d is
+ * deg_h (exact != 0) or the Alg. 1 estimate, every value current for X_q.
+ * Since 2 |E_h(X)| = sum_v deg_h(v; X), sum[q] / (2 size[q]) estimates the
+ * h-density |E_h(X_q)| / |X_q|.  round_of: host int32[n] with values in
+ * [0, rounds), e.g. from kh_peel_info after kh_core_*; one node per round
+ * gives the paper's n candidates.  Outputs (host, each may be NULL):
+ * sum uint64[rounds], size int64[rounds] (|X_q|), *best = the q of largest
+ * sum[q] / size[q] (ties: the smallest q; -1 when n = 0).  Uses the graph's
+ * h and sampling parameters: the paper draws fresh ranks for Alg. 7, which a
+ * caller gets with kh_set_sampling and another seed.  Afterwards kh_peel_info
+ * and kh_peel_stats describe this replay.  KH_EINVAL for a batch, rounds
+ * outside [1, n + 1] or a round_of value outside [0, rounds). */
+int kh_dense(kh_graph *g, int32_t exact, const int32_t *round_of, int32_t rounds, uint64_t *sum,
+             int64_t *size, int32_t *best);
+
 /* Work statistics of the last kh_core_* call (no counterpart in the paper).
  * refreshed[i] / changed[i] (host int64[KH_MAX_H + 1], indexed by level i,
  * each may be NULL): level-i lists recomputed by the rounds' refresh passes

@@ -217,6 +217,8 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.rho);
     dfree(&g.loss);
     dfree(&g.listL);
+    dfree(&g.sched);
+    dfree(&g.dsum);
     dfree(&g.deadbm);
     dfree(&g.gid);
     dfree(&g.vtx_off);
@@ -669,6 +671,48 @@ int kh_peel_info(kh_graph* G, int32_t* round_of, int64_t* rounds, int64_t* updat
         cudaSetDevice(g.ctx->device);
         return kh::copy_out(g, round_of, g.round_of, sizeof(int32_t) * (size_t)g.n, 0);
     }
+    return KH_OK;
+}
+
+int kh_dense(kh_graph* G, int32_t exact, const int32_t* round_of, int32_t rounds, uint64_t* sum,
+             int64_t* size, int32_t* best) {
+    if (!G || !round_of) return KH_EINVAL;
+    Graph& g = G->g;
+    if (g.gid) return kh::set_error(g.ctx, KH_EINVAL, "kh_dense takes a single graph, not a batch");
+    if (rounds < 1 || (int64_t)rounds > g.n + 1)
+        return kh::set_error(g.ctx, KH_EINVAL, "rounds must be in [1, n + 1]");
+    std::vector<int64_t> left((size_t)rounds + 1, 0);
+    for (int64_t v = 0; v < g.n; ++v) {
+        const int32_t r = round_of[v];
+        if (r < 0 || r >= rounds) return kh::set_error(g.ctx, KH_EINVAL, "round_of[%lld] = %d outside [0, rounds)", (long long)v, r);
+        left[(size_t)r] += 1;
+    }
+    for (int32_t q = rounds - 1; q >= 0; --q) left[(size_t)q] += left[(size_t)q + 1];  // |X_q|
+    cudaSetDevice(g.ctx->device);
+    int rc = kh::ensure_work(g);
+    if (rc) return rc;
+    if ((rc = kh::dalloc(g.ctx, &g.sched, (size_t)g.n, "removal order"))) return rc;
+    if ((rc = kh::dalloc(g.ctx, &g.dsum, (size_t)g.n + 1, "per-round sums"))) return rc;
+    if (g.n > 0)
+        KH_CUDA_TRY(g.ctx, cudaMemcpy(g.sched, round_of, sizeof(int32_t) * (size_t)g.n, cudaMemcpyHostToDevice));
+    KH_CUDA_TRY(g.ctx, cudaMemset(g.dsum, 0, sizeof(unsigned long long) * ((size_t)g.n + 1)));
+    g.dense = true;
+    rc = kh::run_core(g, exact == 0, nullptr, nullptr, false);
+    g.dense = false;
+    if (rc) return rc;
+    std::vector<unsigned long long> s((size_t)rounds);
+    KH_CUDA_TRY(g.ctx, cudaMemcpy(s.data(), g.dsum, sizeof(unsigned long long) * (size_t)rounds, cudaMemcpyDeviceToHost));
+    int32_t arg = -1;
+    for (int32_t q = 0; q < rounds; ++q) {
+        if (sum) sum[q] = (uint64_t)s[(size_t)q];
+        if (size) size[q] = left[(size_t)q];
+        if (left[(size_t)q] == 0) continue;
+        // densest: largest sum / size, compared exactly; ties keep the earlier (larger) set
+        if (arg < 0 || (unsigned __int128)s[(size_t)q] * (unsigned __int128)left[(size_t)arg] >
+                           (unsigned __int128)s[(size_t)arg] * (unsigned __int128)left[(size_t)q])
+            arg = q;
+    }
+    if (best) *best = arg;
     return KH_OK;
 }
 

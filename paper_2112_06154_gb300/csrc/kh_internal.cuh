@@ -138,6 +138,10 @@ void launch_gather_last(Graph& g, uint8_t* lvl_out, int32_t* bs_out, cudaStream_
 
 // ---- launchers (kh_peel.cu) --------------------------------------------------
 int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, bool out_dev);
+// EstDense (Alg. 7): replay of a removal order with eager refresh; per round,
+// the sum of d over the alive set (host outputs)
+int run_dense(Graph& g, bool sampled, const int32_t* round_of, int32_t rounds, uint64_t* sum,
+              int64_t* size, int32_t* best);
 int run_estimate_all(Graph& g);
 
 }  // namespace kh
@@ -220,6 +224,10 @@ struct Graph {
     int64_t last_lvl_changed[kMaxH + 1];
     int64_t last_stopped;
     bool have_rounds;
+    // EstDense replay: the removal order (round per node), per-round sums of d
+    bool dense;
+    int32_t* sched;
+    unsigned long long* dsum;
     // profiling: CUDA events around every launch of a kernel class
     bool prof_on;
     std::vector<cudaEvent_t>* ev_pool;

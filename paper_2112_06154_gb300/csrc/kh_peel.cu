@@ -292,6 +292,56 @@ __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict_
     }
 }
 
+// EstDense: the round's candidate set X is the alive set with every value
+// current; its sum of d goes to dsum[round].
+template <typename T>
+__global__ void k_dense_sum(const uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
+                            const DevState* __restrict__ st, unsigned long long* __restrict__ dsum,
+                            int64_t cap) {
+    if (st->n_alive == 0) return;
+    const int round = st->round;
+    if (round >= cap) return;
+    unsigned long long s = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (alive[v] == 1) s += (unsigned long long)d[v];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(kFull, s, off);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(dsum + round, s);
+}
+
+// EstDense: the nodes whose scheduled round has come leave (the removal order
+// is given, not chosen by d).
+__global__ void k_select_sched(uint8_t* __restrict__ alive, const int32_t* __restrict__ sched,
+                               int64_t n, DevState* st, int32_t* __restrict__ R,
+                               int32_t* __restrict__ seen, int32_t* __restrict__ round_of) {
+    if (st->n_alive == 0) return;
+    const int round = st->round;
+    const int lane = threadIdx.x & 31;
+    int keep = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nround = (n + 31) & ~(int64_t)31;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
+        bool rm = false;
+        if (v < n && alive[v] == 1) {
+            if (sched[v] <= round) {
+                rm = true;
+                round_of[v] = round;
+                alive[v] = 2;
+                seen[v] = round * kPhaseStride;
+            } else {
+                ++keep;
+            }
+        }
+        const uint32_t m = __ballot_sync(kFull, rm);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&st->nR, __popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (rm) R[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+    for (int off = 16; off > 0; off >>= 1) keep += __shfl_down_sync(kFull, keep, off);
+    if (lane == 0 && keep) atomicAdd(&st->n_alive_next, keep);
+}
+
 int peel_grid(const Graph& g) {
     int64_t grid = (g.n + kPeelThreads - 1) / kPeelThreads;
     const int64_t gmax = (int64_t)g.ctx->sm_count * 4;
@@ -327,7 +377,7 @@ int refine(Graph& g, bool sampled, cudaStream_t s) {
     prof_end(g, kProfPeel, s);
     if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s, 2);
     return launch_hdeg(g, g.listB, &g.state->nQ, 0, g.d32, nullptr, 0, 0, s,
-                       &g.state->rc[kRcBfs], true);
+                       &g.state->rc[kRcBfs], !g.dense);
 }
 
 // Start of a peel: levels below h in full (sampled), every node stale with its
@@ -359,10 +409,66 @@ int start_peel(Graph& g, bool sampled, cudaStream_t s) {
     return KH_OK;
 }
 
+// The second half of a round: the refresh of the nodes the removal set R
+// affects, then the end of the round.
+int refresh_and_finish(Graph& g, bool sampled, cudaStream_t s) {
+    const int grid = peel_grid(g);
+    const PeelState ps = peel_state(g);
+    int rc = KH_OK;
+    if (!sampled) {
+        // the ball of R in the old graph: alive degrees drop (hop 1), the
+        // nodes within h-1 hops become stale with new lower bounds ...
+        const int hops = g.hmax > 2 ? g.hmax - 1 : 1;
+        for (int hop = 1; hop <= hops; ++hop) launch_ball_hop(g, hop, s);
+        launch_stale_exact(g, g.listW, &g.state->rc[kRcW], s);
+        // ... and the nodes exactly h hops away lose exactly the removed nodes
+        // within h hops: their values (and bounds) are decremented in place
+        rc = launch_hdeg(g, g.listR, &g.state->nR, 0, g.d32, nullptr, 0, 0, s,
+                         &g.state->rc[kRcLossWork], false, true);
+        if (rc) return rc;
+        launch_apply_loss(g, s);
+    } else {
+        int* rcs = g.state->rc;
+        for (int i = 1; i <= g.hmax && rc == KH_OK; ++i) {
+            // level i candidates: A(R), plus A(nodes whose level i-1 changed)
+            launch_mark_neighbours(g, g.listR, &g.state->nR, i >= 2 ? g.listC[(i - 1) & 1] : nullptr,
+                                   rcs + kRcC + i - 1, i, rcs + kRcW + i, s);
+            // nodes with more levels recompute level i (tracking changes) ...
+            if (i < g.hmax) rc = launch_level(g, i, g.listW, rcs + kRcW + i, 0, 1, s, 1);
+            // ... nodes whose last level is i become stale (lazy refine)
+            if (i >= g.hmin) launch_stale_sampled(g, g.listW, rcs + kRcW + i, s, i);
+        }
+        if (rc) return rc;
+    }
+    prof_begin(g, kProfPeel, s);
+    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm, ps, peel_graphs(g));
+    count_launch(g, 1);
+    prof_end(g, kProfPeel, s);
+    return KH_OK;
+}
+
 // One peeling round, entirely stream-ordered (capturable).
 int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     const int grid = peel_grid(g);
     int rc = KH_OK;
+    if (g.dense) {
+        // EstDense: the threshold stays infinite (no round minimum is taken),
+        // so every stale node is recomputed in full before the sum is taken
+        rc = refine(g, sampled, s);
+        if (rc) return rc;
+        prof_begin(g, kProfPeel, s);
+        if (sampled)
+            k_dense_sum<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
+                                                                         g.dsum, g.n + 1);
+        else
+            k_dense_sum<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state, g.dsum,
+                                                               g.n + 1);
+        k_select_sched<<<grid, kPeelThreads, 0, s>>>(g.alive, g.sched, g.n, g.state, g.listR, g.seen,
+                                                     g.round_of);
+        count_launch(g, 2);
+        prof_end(g, kProfPeel, s);
+        return refresh_and_finish(g, sampled, s);
+    }
     // U = min of the upper bounds; refine stale nodes with lb <= max(c, U)
     prof_begin(g, kProfPeel, s);
     if (sampled)
@@ -398,36 +504,7 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
         count_launch(g, 1);
     }
     prof_end(g, kProfPeel, s);
-    if (!sampled) {
-        // the ball of R in the old graph: alive degrees drop (hop 1), the
-        // nodes within h-1 hops become stale with new lower bounds ...
-        const int hops = g.hmax > 2 ? g.hmax - 1 : 1;
-        for (int hop = 1; hop <= hops; ++hop) launch_ball_hop(g, hop, s);
-        launch_stale_exact(g, g.listW, &g.state->rc[kRcW], s);
-        // ... and the nodes exactly h hops away lose exactly the removed nodes
-        // within h hops: their values (and bounds) are decremented in place
-        rc = launch_hdeg(g, g.listR, &g.state->nR, 0, g.d32, nullptr, 0, 0, s,
-                         &g.state->rc[kRcLossWork], false, true);
-        if (rc) return rc;
-        launch_apply_loss(g, s);
-    } else {
-        int* rcs = g.state->rc;
-        for (int i = 1; i <= g.hmax && rc == KH_OK; ++i) {
-            // level i candidates: A(R), plus A(nodes whose level i-1 changed)
-            launch_mark_neighbours(g, g.listR, &g.state->nR, i >= 2 ? g.listC[(i - 1) & 1] : nullptr,
-                                   rcs + kRcC + i - 1, i, rcs + kRcW + i, s);
-            // nodes with more levels recompute level i (tracking changes) ...
-            if (i < g.hmax) rc = launch_level(g, i, g.listW, rcs + kRcW + i, 0, 1, s, 1);
-            // ... nodes whose last level is i become stale (lazy refine)
-            if (i >= g.hmin) launch_stale_sampled(g, g.listW, rcs + kRcW + i, s, i);
-        }
-        if (rc) return rc;
-    }
-    prof_begin(g, kProfPeel, s);
-    k_finish<<<grid, kPeelThreads, 0, s>>>(g.alive, g.listR, g.state, g.deadbm, ps, peel_graphs(g));
-    count_launch(g, 1);
-    prof_end(g, kProfPeel, s);
-    return KH_OK;
+    return refresh_and_finish(g, sampled, s);
 }
 
 int check_state_err(Graph& g, const DevState& hs) {
@@ -439,7 +516,7 @@ int check_state_err(Graph& g, const DevState& hs) {
 // Capture kRoundsPerGraph rounds into an executable graph (cached per shape).
 int round_graph(Graph& g, bool sampled, cudaStream_t s, cudaGraphExec_t* out) {
     // everything a captured launch bakes in: mode, h, M, slot size, scratch, batch tables
-    const int key[8] = {sampled ? 1 : 0, g.h, (int)g.M, (int)g.cap, (int)g.scratch_ctas,
+    const int key[8] = {(sampled ? 1 : 0) | (g.dense ? 2 : 0), g.h, (int)g.M, (int)g.cap, (int)g.scratch_ctas,
                         (int)(reinterpret_cast<uintptr_t>(g.hv) >> 4),
                         (int)(reinterpret_cast<uintptr_t>(g.Mv) >> 4), g.hmin};
     if (g.round_exec && memcmp(key, g.round_exec_key, sizeof(key)) == 0) {
@@ -573,7 +650,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     g.have_rounds = true;
     const size_t bytes = (size_t)g.n * (sampled ? sizeof(unsigned long long) : sizeof(int32_t));
     const void* src = sampled ? (const void*)g.core64 : (const void*)g.core32;
-    if (g.n > 0)
+    if (g.n > 0 && out_core)
         KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(out_core, src, bytes,
                                            out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (!out_dev) KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("kh_prof_read", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _I64P,
                                     ctypes.POINTER(ctypes.c_double)]),
     ("kh_peel_stats", ctypes.c_int, [_P, _P, _P, _I64P]),
+    ("kh_dense", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
+                                ctypes.POINTER(ctypes.c_int32)]),
     ("kh_prof_trace", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -275,6 +277,19 @@ def kh_peel_info(g: Graph, want_rounds: bool = True):
 
 
 KH_MAX_H = 16
+
+
+def kh_dense(g: Graph, exact: bool, round_of, rounds: int):
+    """EstDense (Alg. 7): (sum uint64[rounds], size int64[rounds], best)."""
+    ro = np.ascontiguousarray(round_of, dtype=np.int32)
+    if ro.size != g.n:
+        raise KhError(KH_EINVAL, f"round_of has {ro.size} entries, the graph {g.n} nodes")
+    total = np.zeros(max(rounds, 1), np.uint64)
+    size = np.zeros(max(rounds, 1), np.int64)
+    best = ctypes.c_int32(-1)
+    _check(load().kh_dense(g.handle, 1 if exact else 0, ro.ctypes.data, rounds, total.ctypes.data,
+                           size.ctypes.data, ctypes.byref(best)), g.ctx)
+    return total[:rounds], size[:rounds], int(best.value)
 
 
 def kh_peel_stats(g: Graph):
