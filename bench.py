@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
                                     "sampled3", "exact2"],
                    help="run one operation of the step once (a target for profilers) and exit")
-    p.add_argument("--workload", choices=["chung_lu", "batch", "serve", "rmat", "dense"],
+    p.add_argument("--workload", choices=["chung_lu", "batch", "serve", "rmat", "dense", "sweep"],
                    default="chung_lu",
                    help="batch: 4096 preferential-attachment graphs, batched vs one graph per call; "
                         "serve: a Poisson request stream through the continuous-batching server")
@@ -492,6 +492,65 @@ def run_dense(args):
     ctx.close()
 
 
+def run_sweep(args):
+    """Analogues of Fig. 1 and Fig. 2 (Sec. 8.2, 8.3), on seeded synthetic graphs.
+    (1) eps sweep: M from Eq. (buffer); the sampled (k,h)-core's time and its
+    relative error |c'(v) - c(v)| / c(v) against the exact core (maximum, the
+    paper's measure, and mean) on the Chung-Lu n=200k graph (h=2) and a Chung-Lu
+    n=20k graph (h=3).  (2) hierarchical SBM, n = 10k..100k, h = 2, 3, 4 at
+    eps = 0.5: the sampled core's time against the number of edges."""
+    import torch
+    from paper_2112_06154_gb300 import graphgen as gg
+    from paper_2112_06154_gb300 import khcore as K
+    K.load()
+    ctx = K.kh_ctx_create(0)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    out = {"workload": "eps_sweep_and_sbm", "impl": "ours", "unit": "s", "higher_is_better": False,
+           "eps_sweep": [], "sbm": []}
+    cases = [("chung_lu_n200k", make_graph(), 2, (0.5, 0.35, 0.25)),
+             ("chung_lu_n20k", gg.chung_lu(20000, 20, 2.5, 1000, 1102), 3,
+              (0.5, 0.4, 0.3, 0.2, 0.15))]
+    for name, (rowptr, col), h, eps_list in cases:
+        G = K.kh_graph_load_csr(ctx, rowptr, col)
+        K.kh_set_h(G, h)
+        K.kh_core_exact(G)  # warm-up
+        exact, t_exact = timed(lambda: K.kh_core_exact(G))
+        exact = exact.astype(np.float64)
+        pos = exact > 0
+        for eps in eps_list:
+            K.kh_set_sampling(G, seed=1, M=0, eps=eps, delta=0.05)
+            sampled, secs = timed(lambda: K.kh_core_sampled(G))
+            rel = np.abs(sampled.astype(np.float64)[pos] - exact[pos]) / exact[pos]
+            out["eps_sweep"].append({
+                "graph": name, "h": h, "eps": eps, "M": K.kh_get_M(G), "sampled_core_s": secs,
+                "exact_core_s": t_exact, "max_rel_err": float(rel.max()) if rel.size else 0.0,
+                "mean_rel_err": float(rel.mean()) if rel.size else 0.0,
+                "frac_above_eps": float((rel > eps).mean()) if rel.size else 0.0,
+                "zero_core_mismatches": int((sampled[~pos] != 0).sum())})
+        G.close()
+    for n in (10000, 25000, 50000, 100000):
+        rowptr, col = gg.sbm_hierarchical(n, 1007)
+        G = K.kh_graph_load_csr(ctx, rowptr, col)
+        K.kh_set_sampling(G, seed=1)
+        row = {"n": n, "m": int(col.size // 2), "M": K.kh_get_M(G)}
+        for h in (2, 3, 4):
+            K.kh_set_h(G, h)
+            K.kh_core_sampled(G)  # warm-up
+            _, secs = timed(lambda: K.kh_core_sampled(G))
+            row[f"h{h}_s"] = secs
+        out["sbm"].append(row)
+        G.close()
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_batch(args):
     """Batched workload: many preferential-attachment graphs (n log-uniform in
     [100, 20000], m uniform in {3..8}, h uniform in {2,3,4}, per-graph M).
@@ -649,6 +708,8 @@ def main():
         run_rmat(args)
     elif args.workload == "dense" and args.impl == "ours":
         run_dense(args)
+    elif args.workload == "sweep" and args.impl == "ours":
+        run_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -77,6 +77,35 @@ def erdos_renyi(n: int, m: int, seed: int):
     return csr_from_edges(n, i, j)
 
 
+def sbm_hierarchical(n: int, seed: int, blocks: int = 10, base: float = 1e-6):
+    """Stochastic block model with `blocks` equal blocks C_1..C_b (block i holds
+    nodes [(i-1) n/b, i n/b)); a pair in C_i x C_j, i <= j, is an edge with
+    probability base * i^2 (the within-block probability uses i = j).  The
+    number of edges of each block pair is binomial; the pairs are drawn
+    uniformly and de-duplicated."""
+    rng = np.random.default_rng(seed)
+    bounds = [(q * n) // blocks for q in range(blocks + 1)]
+    us, vs = [], []
+    for i in range(1, blocks + 1):
+        lo_i, hi_i = bounds[i - 1], bounds[i]
+        for j in range(i, blocks + 1):
+            lo_j, hi_j = bounds[j - 1], bounds[j]
+            a, b = hi_i - lo_i, hi_j - lo_j
+            pairs = a * (a - 1) // 2 if i == j else a * b
+            if pairs <= 0:
+                continue
+            k = int(rng.binomial(pairs, min(1.0, base * i * i)))
+            if k == 0:
+                continue
+            u = rng.integers(lo_i, hi_i, size=k, dtype=np.int64)
+            v = rng.integers(lo_j, hi_j, size=k, dtype=np.int64)
+            us.append(u)
+            vs.append(v)
+    if not us:
+        return csr_from_edges(n, np.empty(0, np.int64), np.empty(0, np.int64))
+    return csr_from_edges(n, np.concatenate(us), np.concatenate(vs))
+
+
 def chung_lu(n: int, avg_deg: float, gamma: float, max_deg: int, seed: int):
     """Chung-Lu power-law graph with expected degrees w_i (see module doc)."""
     rng = np.random.default_rng(seed)
