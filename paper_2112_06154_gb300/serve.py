@@ -6,6 +6,9 @@ device-memory footprint fits in the budget next to the requests already on
 the GPU; each slot owns a library context with its own CUDA stream, so the
 admitted requests' kernels overlap on the device.  Requests are admitted in
 arrival order; one that can never fit the budget is rejected at submission.
+A queued request can be cancelled (Future.cancel) or carry a deadline: one
+still waiting when its deadline passes fails with TimeoutError and is never
+started.  A started request runs to completion.
 
 Every result is the deterministic function of (graph, h, seed, M) that
 kh_core_sampled computes, so a request returns the same core numbers alone
@@ -57,6 +60,7 @@ class Request:
     future: Future = field(default_factory=Future)
     admitted: float = 0.0
     finished: float = 0.0
+    deadline: float | None = None  # perf_counter time by which it must start
 
 
 def gpu_runner(device: int = 0):
@@ -102,13 +106,15 @@ class KhServer:
         self.closing = False
         self.next_id = 0
         self.done: list[Request] = []
+        self.dropped = 0  # cancelled or past their deadline before admission
         self.workers = [threading.Thread(target=self._worker, args=(runner_factory,), daemon=True)
                         for _ in range(slots)]
         for w in self.workers:
             w.start()
 
     def submit(self, rowptr, col, h: int, seed: int = 1, M: int = 0, eps: float = 0.5,
-               delta: float = 0.05, arrival: float | None = None) -> Future:
+               delta: float = 0.05, arrival: float | None = None,
+               deadline: float | None = None) -> Future:
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         col = np.ascontiguousarray(col, dtype=np.int32)
         n = int(rowptr.size - 1)
@@ -116,6 +122,7 @@ class KhServer:
         with self.cv:
             req = Request(self.next_id, rowptr, col, h, seed, M, eps, delta,
                           arrival if arrival is not None else time.perf_counter())
+            req.deadline = deadline
             self.next_id += 1
             req.footprint = footprint_bytes(n, int(col.size), h, Mv)
             if req.footprint > self.mem_budget:
@@ -126,10 +133,31 @@ class KhServer:
             self.cv.notify_all()
         return req.future
 
+    def _drop_expired(self):
+        # cancelled heads leave; heads past their deadline fail without starting
+        now = time.perf_counter()
+        while self.queue:
+            head = self.queue[0]
+            if head.future.cancelled():
+                self.queue.popleft()
+                self.dropped += 1
+            elif head.deadline is not None and now > head.deadline:
+                self.queue.popleft()
+                self.dropped += 1
+                if head.future.set_running_or_notify_cancel():
+                    head.future.set_exception(TimeoutError(
+                        f"request {head.rid} not started before its deadline"))
+            else:
+                return
+
     def _admit(self) -> Request | None:
         # arrival order: the head is admitted when it fits
+        self._drop_expired()
         if self.queue and self.mem_in_use + self.queue[0].footprint <= self.mem_budget:
             req = self.queue.popleft()
+            if not req.future.set_running_or_notify_cancel():
+                self.dropped += 1  # cancelled between the check and now
+                return None
             self.mem_in_use += req.footprint
             self.running += 1
             self.peak_mem = max(self.peak_mem, self.mem_in_use)

@@ -91,3 +91,58 @@ def test_failed_request_does_not_stop_the_server():
     srv.close()
     st = srv.latency_stats()
     assert st["requests"] == 5 and st["p99_s"] >= st["p50_s"] >= 0
+
+
+def test_cancelled_request_never_starts():
+    log = []
+    srv = S.KhServer(fake_factory(log, delay=0.05), slots=1, mem_budget=1 << 40)
+    rp, cl = gg.path(30)
+    futs = [srv.submit(rp, cl, h=2) for _ in range(4)]
+    assert futs[2].cancel()  # still queued behind the first request
+    assert [futs[q].result(timeout=10)["rid"] for q in (0, 1, 3)] == [0, 1, 3]
+    srv.close()
+    assert futs[2].cancelled()
+    assert 2 not in [rid for kind, rid in log if kind == "start"]
+    assert srv.dropped == 1 and srv.mem_in_use == 0 and srv.running == 0
+
+
+def test_deadline_fails_a_request_that_waits_too_long():
+    log = []
+    srv = S.KhServer(fake_factory(log, delay=0.2), slots=1, mem_budget=1 << 40)
+    rp, cl = gg.path(30)
+    first = srv.submit(rp, cl, h=2)
+    late = srv.submit(rp, cl, h=2, deadline=time.perf_counter() + 0.05)
+    relaxed = srv.submit(rp, cl, h=2, deadline=time.perf_counter() + 60.0)
+    with pytest.raises(TimeoutError):
+        late.result(timeout=10)
+    assert first.result(timeout=10)["rid"] == 0
+    assert relaxed.result(timeout=10)["rid"] == 2
+    srv.close()
+    assert 1 not in [rid for kind, rid in log if kind == "start"]
+    assert srv.dropped == 1
+
+
+def test_concurrent_clients():
+    # several client threads submit at once; every result reaches its caller
+    log = []
+    srv = S.KhServer(fake_factory(log, delay=0.002), slots=3, mem_budget=1 << 40)
+    graphs = [gg.path(10 + k) for k in range(8)]
+    results = {}
+    lock = threading.Lock()
+
+    def client(k):
+        rp, cl = graphs[k]
+        fs = [srv.submit(rp, cl, h=2) for _ in range(10)]
+        got = [f.result(timeout=30)["n"] for f in fs]
+        with lock:
+            results[k] = got
+
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    srv.close()
+    for k in range(8):
+        assert results[k] == [10 + k] * 10
+    assert len(srv.done) == 80 and srv.mem_in_use == 0 and srv.peak_running <= 3
