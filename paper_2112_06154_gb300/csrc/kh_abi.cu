@@ -429,12 +429,14 @@ static int load_graph(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32
 
 int kh_graph_load_csr(kh_ctx* ctx, int64_t n, const int64_t* rowptr, const int32_t* col,
                       uint32_t flags, kh_graph** out) {
+    kh::NvtxRange nvtx_range("kh_graph_load_csr");
     return kh::load_graph(ctx, n, rowptr, col, flags, nullptr, out);
 }
 
 int kh_graph_load_batch(kh_ctx* ctx, int32_t ngraphs, const int64_t* vtx_off, const int64_t* rowptr,
                         const int32_t* col, const int32_t* h_per_graph, uint32_t flags,
                         kh_graph** out) {
+    kh::NvtxRange nvtx_range("kh_graph_load_batch");
     if (!ctx || !out || ngraphs < 1 || !vtx_off) return KH_EINVAL;
     *out = nullptr;
     if (vtx_off[0] != 0) return kh::set_error(ctx, KH_EINVAL, "vtx_off[0] must be 0");
@@ -584,6 +586,7 @@ int kh_ranks(kh_graph* G, uint8_t* r, uint32_t flags) {
 }
 
 int kh_hdegree_exact(kh_graph* G, int32_t* deg, uint32_t flags) {
+    kh::NvtxRange nvtx_range("kh_hdegree_exact");
     if (!G || (!deg && G->g.n > 0)) return KH_EINVAL;
     Graph& g = G->g;
     cudaSetDevice(g.ctx->device);
@@ -601,6 +604,7 @@ int kh_hdegree_exact(kh_graph* G, int32_t* deg, uint32_t flags) {
 }
 
 int kh_sampled_counts(kh_graph* G, int32_t j_lo, int32_t j_hi, int32_t* cnt, uint32_t flags) {
+    kh::NvtxRange nvtx_range("kh_sampled_counts");
     if (!G || (!cnt && G->g.n > 0)) return KH_EINVAL;
     Graph& g = G->g;
     if (j_lo < 0 || j_hi > 31 || j_lo > j_hi)
@@ -633,6 +637,7 @@ int kh_sampled_counts(kh_graph* G, int32_t j_lo, int32_t j_hi, int32_t* cnt, uin
 }
 
 int kh_estimate(kh_graph* G, uint64_t* est, uint8_t* level, int32_t* bsize, uint32_t flags) {
+    kh::NvtxRange nvtx_range("kh_estimate");
     if (!G || (!est && G->g.n > 0)) return KH_EINVAL;
     Graph& g = G->g;
     cudaSetDevice(g.ctx->device);
@@ -650,12 +655,14 @@ int kh_estimate(kh_graph* G, uint64_t* est, uint8_t* level, int32_t* bsize, uint
 }
 
 int kh_core_exact(kh_graph* G, int32_t* core, uint32_t flags) {
+    kh::NvtxRange nvtx_range("kh_core_exact");
     if (!G || (!core && G->g.n > 0)) return KH_EINVAL;
     cudaSetDevice(G->g.ctx->device);
     return kh::run_core(G->g, false, core, nullptr, (flags & KH_DEVICE_PTR) != 0);
 }
 
 int kh_core_sampled(kh_graph* G, uint64_t* core, uint32_t flags) {
+    kh::NvtxRange nvtx_range("kh_core_sampled");
     if (!G || (!core && G->g.n > 0)) return KH_EINVAL;
     cudaSetDevice(G->g.ctx->device);
     return kh::run_core(G->g, true, core, nullptr, (flags & KH_DEVICE_PTR) != 0);
@@ -676,6 +683,7 @@ int kh_peel_info(kh_graph* G, int32_t* round_of, int64_t* rounds, int64_t* updat
 
 int kh_dense(kh_graph* G, int32_t exact, const int32_t* round_of, int32_t rounds, uint64_t* sum,
              int64_t* size, int32_t* best) {
+    kh::NvtxRange nvtx_range("kh_dense");
     if (!G || !round_of) return KH_EINVAL;
     Graph& g = G->g;
     if (g.gid) return kh::set_error(g.ctx, KH_EINVAL, "kh_dense takes a single graph, not a batch");

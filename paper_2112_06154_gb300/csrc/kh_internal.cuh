@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/khcore.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace kh {
 
@@ -91,6 +92,14 @@ struct DevState {
 };
 
 struct Graph;
+
+// NVTX range for profilers and tracers (a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- launchers (kh_exact.cu) -------------------------------------------------
 void launch_ranks(const Graph& g, cudaStream_t s);

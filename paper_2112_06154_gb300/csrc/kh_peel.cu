@@ -622,6 +622,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
         if (rc) return rc;
     }
     for (;;) {
+        NvtxRange nvtx_range(use_graph ? "peel rounds (graph replay)" : "peel round");
         if (use_graph) {
             KH_CUDA_TRY(g.ctx, cudaGraphLaunch(exec, s));
             launches += kRoundsPerGraph;
