@@ -60,6 +60,13 @@ int kh_ctx_destroy(kh_ctx *ctx);
 /* Text of the last error reported by a call on `ctx` (never NULL). */
 const char *kh_last_error(kh_ctx *ctx);
 
+/* Fault injection on the host (no counterpart in the paper; a test aid): the
+ * k-th device allocation this context makes after the call fails with
+ * KH_ENOMEM, once; k = 0 disarms.  A failed call leaves the graph and the
+ * context usable: a later call allocates what is missing.  KH_EINVAL for a
+ * NULL context or k < 0. */
+int kh_debug_fail_alloc(kh_ctx *ctx, int64_t k);
+
 /* Load a graph (Sec. 2: G = (V, E), n nodes, undirected).  rowptr has n+1
  * int64 entries, col has rowptr[n] int32 entries.  The library copies both
  * into device memory it owns; the caller keeps ownership of its arrays.

@@ -33,6 +33,10 @@ int check_cuda(kh_ctx* ctx, cudaError_t e, const char* what) {
 template <typename T>
 static int dalloc(kh_ctx* ctx, T** p, size_t count, const char* what) {
     if (*p) return KH_OK;
+    if (ctx->fail_alloc_at > 0 && ++ctx->alloc_count == ctx->fail_alloc_at) {
+        ctx->fail_alloc_at = 0;  // one failure per arming
+        return set_error(ctx, KH_ENOMEM, "%s: injected allocation failure", what);
+    }
     if (count == 0) count = 1;
     cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
     if (e != cudaSuccess) {
@@ -322,6 +326,13 @@ int kh_ctx_destroy(kh_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
+    return KH_OK;
+}
+
+int kh_debug_fail_alloc(kh_ctx* ctx, int64_t k) {
+    if (!ctx || k < 0) return KH_EINVAL;
+    ctx->fail_alloc_at = k;
+    ctx->alloc_count = 0;
     return KH_OK;
 }
 

@@ -161,6 +161,10 @@ struct kh_ctx {
     bool own_stream;
     int sm_count;
     char err[512];
+    // fault injection on the host: the fail_alloc_at-th device allocation from
+    // the arming call fails with KH_ENOMEM (0: off)
+    int64_t fail_alloc_at;
+    int64_t alloc_count;
 };
 
 namespace kh {

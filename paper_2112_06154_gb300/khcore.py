@@ -42,6 +42,7 @@ SIGNATURES = [
     ("kh_ctx_create", ctypes.c_int, [_PP, ctypes.c_int, _P]),
     ("kh_ctx_destroy", ctypes.c_int, [_P]),
     ("kh_last_error", ctypes.c_char_p, [_P]),
+    ("kh_debug_fail_alloc", ctypes.c_int, [_P, ctypes.c_int64]),
     ("kh_graph_load_csr", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_uint32, _PP]),
     ("kh_graph_free", ctypes.c_int, [_P]),
     ("kh_graph_load_batch", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_uint32, _PP]),
@@ -167,6 +168,13 @@ def kh_ctx_create(device: int = 0, stream=None) -> Ctx:
 
 def kh_ctx_destroy(ctx: Ctx):
     ctx.close()
+
+
+def kh_debug_fail_alloc(ctx: Ctx, k: int):
+    """Make the k-th device allocation of this context fail once with KH_ENOMEM (0: off)."""
+    rc = load().kh_debug_fail_alloc(ctx.handle, k)
+    if rc:
+        raise KhError(rc, "kh_debug_fail_alloc")
 
 
 def kh_last_error(ctx: Ctx) -> str:
