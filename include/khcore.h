@@ -25,7 +25,11 @@
  *   - Output arrays are caller-allocated.  Without KH_DEVICE_PTR they are host
  *     memory and the call returns after the results are written.  With
  *     KH_DEVICE_PTR they are device memory of the context's device and the
- *     call only enqueues work on the context's stream (kh_sync waits).
+ *     results are written by work enqueued on the context's stream (kh_sync
+ *     waits): kh_ranks, kh_hdegree_exact, kh_sampled_counts and kh_estimate
+ *     only enqueue; the peels (kh_core_*, kh_dense) read a small device state
+ *     once per eight rounds to know when to stop, so they synchronize with the
+ *     stream while they run and enqueue only the final copy.
  *   - Every result is a deterministic function of (graph, h, seed, M).
  *   - A context and its graphs must be used from one host thread at a time.
  */
