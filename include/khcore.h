@@ -26,10 +26,11 @@
  *     memory and the call returns after the results are written.  With
  *     KH_DEVICE_PTR they are device memory of the context's device and the
  *     results are written by work enqueued on the context's stream (kh_sync
- *     waits): kh_ranks, kh_hdegree_exact, kh_sampled_counts and kh_estimate
- *     only enqueue; the peels (kh_core_*, kh_dense) read a small device state
- *     once per eight rounds to know when to stop, so they synchronize with the
- *     stream while they run and enqueue only the final copy.
+ *     waits): kh_ranks, kh_hdegree_exact and kh_sampled_counts only enqueue;
+ *     kh_estimate waits for its device error word before returning; the peels
+ *     (kh_core_*, kh_dense) read a small device state once per eight rounds
+ *     to know when to stop, so they synchronize with the stream while they run
+ *     and enqueue only the final copy.
  *   - Every result is a deterministic function of (graph, h, seed, M).
  *   - A context and its graphs must be used from one host thread at a time.
  */
