@@ -81,6 +81,7 @@ int ensure_work(Graph& g) {
     const size_t ng = (size_t)(g.gid ? g.ngraphs : 1);
     if ((rc = dalloc(g.ctx, &g.pc, ng, "per-graph c"))) return rc;
     if ((rc = dalloc(g.ctx, &g.pmn, ng, "per-graph minimum"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.pmr, ng, "per-graph refined minimum"))) return rc;
     if ((rc = dalloc(g.ctx, &g.pmu, ng, "per-graph threshold"))) return rc;
     if ((rc = dalloc(g.ctx, &g.pleft, ng, "per-graph alive count"))) return rc;
     return KH_OK;
@@ -228,6 +229,7 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.vtx_off);
     dfree(&g.pc);
     dfree(&g.pmn);
+    dfree(&g.pmr);
     dfree(&g.pmu);
     dfree(&g.pleft);
     dfree(&g.hv);

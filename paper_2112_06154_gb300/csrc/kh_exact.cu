@@ -117,6 +117,7 @@ struct BfsArgs {
     unsigned long long* lb;
     uint8_t* fresh;
     unsigned long long* stopped;  // early-stop count
+    unsigned long long* min_done;  // refine: per-graph minimum of the completed values
     // loss mode (nullptr: off): per-node loss counters and their list, the
     // ball stamps of the round and where the round index lives
     int32_t* loss;
@@ -351,6 +352,8 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 atomicAdd(a.stopped, 1ull);
             } else {
                 a.deg[v] = s_count;
+                if (a.min_done)
+                    atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), (unsigned long long)s_count);
             }
             atomicAdd(a.updates, 1ull);
             my_bytes += 4ull + (RANKS ? 4ull * (unsigned long long)a.nj : 0ull);
@@ -584,6 +587,7 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     a.vtx_off = g.vtx_off;
     a.hv = g.hv;
     const bool stop = early_stop && !cnt && !loss;
+    a.min_done = (stop && !g.dense) ? g.pmr : nullptr;
     if (loss) {
         a.loss = g.loss;
         a.loss_list = g.listL;

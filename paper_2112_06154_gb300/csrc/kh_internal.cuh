@@ -211,7 +211,9 @@ struct Graph {
     int32_t *Mv;            // per-node M (nullptr: g.M for every node)
     int64_t ngraphs;
     int64_t max_gn;         // largest graph of the batch
-    unsigned long long *pc, *pmn, *pmu;  // per-graph c, round minimum, refine threshold
+    // per graph: c, round-start minimum over fresh nodes, refine threshold,
+    // minimum of the values the round's refine completed
+    unsigned long long *pc, *pmn, *pmu, *pmr;
     int32_t *pleft;         // per-graph alive count (batches)
     int hmin, hmax;         // range of h over the nodes
     std::vector<int64_t>* h_vtx_off;  // host copy of vtx_off (per-graph M)

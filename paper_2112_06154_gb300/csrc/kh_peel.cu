@@ -51,12 +51,19 @@ constexpr int kRoundsPerGraph = 8;
 
 // Per-graph peel state (a single graph has one entry; a batch one per graph,
 // so each graph peels with its own c exactly as it would alone):
-//   c[g]   core value reached so far, mn[g] this round's minimum of d,
-//   mu[g]  this round's minimum of the upper bounds (lazy refine threshold).
+//   c[g]   core value reached so far,
+//   mu[g]  this round's minimum of d over the alive nodes, fresh or not
+//          (the lazy refine threshold is max(c, mu)),
+//   mn[g]  the same minimum over the fresh nodes only,
+//   mr[g]  the minimum of the values the round's refine completed.
+// The round's minimum of d after the refine is min(mn, mr): a node attaining
+// mu is fresh, or stale with lb <= d = mu and so refined to a value <= mu;
+// every node left stale has d >= lb > max(c, mu).
 struct PeelState {
     unsigned long long* c;
     unsigned long long* mn;
     unsigned long long* mu;
+    unsigned long long* mr;
     int32_t* left;       // alive nodes per graph (batches: per-graph early stop)
     const int32_t* gid;  // graph of each node; nullptr for a single graph
 };
@@ -65,39 +72,59 @@ __device__ __forceinline__ int graph_of(const PeelState& p, int64_t v) {
     return p.gid ? p.gid[v] : 0;
 }
 
-// Minimum of x over a node set into target[graph]: a single graph reduces
-// per block; a batch takes one atomic per node that improves its graph's
-// current minimum (read first, so most nodes need none).
+__device__ __forceinline__ unsigned long long round_min(const PeelState& p, int g) {
+    return p.mn[g] < p.mr[g] ? p.mn[g] : p.mr[g];
+}
+
+__device__ __forceinline__ unsigned long long umin(unsigned long long a, unsigned long long b) {
+    return a < b ? a : b;
+}
+
+// Round start: the minimum of d over the alive nodes into mu[graph] and over
+// the fresh ones into mn[graph].  A single graph reduces per block; a batch
+// takes one atomic per node that improves its graph's current minimum (read
+// first, so most nodes need none).
 template <typename T>
-__global__ void k_min_alive(const uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
-                            DevState* st, unsigned long long* target, const int32_t* __restrict__ gid) {
+__global__ void k_min_alive(const uint8_t* __restrict__ alive, const uint8_t* __restrict__ fresh,
+                            const T* __restrict__ d, int64_t n, DevState* st,
+                            unsigned long long* mu, unsigned long long* mn,
+                            const int32_t* __restrict__ gid) {
     if (st->n_alive == 0) return;
-    unsigned long long m = ~0ull;
+    unsigned long long m = ~0ull, mf = ~0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
         if (alive[v] == 1) {
             const unsigned long long x = (unsigned long long)d[v];
+            const bool fr = fresh[v] != 0;
             if (gid) {
                 const int g = gid[v];
-                if (x < *(volatile unsigned long long*)(target + g)) atomicMin(target + g, x);
-            } else if (x < m) {
-                m = x;
+                if (x < *(volatile unsigned long long*)(mu + g)) atomicMin(mu + g, x);
+                if (fr && x < *(volatile unsigned long long*)(mn + g)) atomicMin(mn + g, x);
+            } else {
+                m = umin(m, x);
+                if (fr) mf = umin(mf, x);
             }
         }
     if (gid) return;
     for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_down_sync(kFull, m, off);
-        if (o < m) m = o;
+        m = umin(m, __shfl_down_sync(kFull, m, off));
+        mf = umin(mf, __shfl_down_sync(kFull, mf, off));
     }
-    __shared__ unsigned long long s_m[kPeelThreads / 32];
+    __shared__ unsigned long long s_m[kPeelThreads / 32], s_f[kPeelThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_m[warp] = m;
+    if (lane == 0) {
+        s_m[warp] = m;
+        s_f[warp] = mf;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            if (s_m[w] < m) m = s_m[w];
-        if (m != ~0ull) atomicMin(target, m);
-        if (blockIdx.x == 0) atomicAdd(&st->bytes[kProfPeel], (unsigned long long)n * (1 + sizeof(T)));
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            m = umin(m, s_m[w]);
+            mf = umin(mf, s_f[w]);
+        }
+        if (m != ~0ull) atomicMin(mu, m);
+        if (mf != ~0ull) atomicMin(mn, mf);
+        if (blockIdx.x == 0) atomicAdd(&st->bytes[kProfPeel], (unsigned long long)n * (2 + sizeof(T)));
     }
 }
 
@@ -179,7 +206,8 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
         bool rm = false;
         if (v < n && alive[v] == 1) {
             const int g = graph_of(p, v);
-            const unsigned long long c = p.c[g] > p.mn[g] ? p.c[g] : p.mn[g];
+            const unsigned long long m = round_min(p, g);
+            const unsigned long long c = p.c[g] > m ? p.c[g] : m;
             if ((unsigned long long)d[v] <= c) {
                 rm = true;
                 if (p.gid) atomicSub(p.left + g, 1);
@@ -211,7 +239,8 @@ __global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* 
                               C* __restrict__ core, int32_t* __restrict__ round_of) {
     if (st->n_alive == 0) return;
     // single graphs only (a batch has no global early stop)
-    const unsigned long long c = p.c[0] > p.mn[0] ? p.c[0] : p.mn[0];
+    const unsigned long long m = round_min(p, 0);
+    const unsigned long long c = p.c[0] > m ? p.c[0] : m;
     const int left = st->n_alive_next;
     const bool early = left > 0 && c + 1 >= (unsigned long long)left;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->early = early ? 1 : 0;
@@ -239,7 +268,8 @@ __global__ void k_assign_rest_batch(uint8_t* __restrict__ alive, int64_t n, DevS
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
         if (alive[v] == 1) {
             const int g = p.gid[v];
-            const unsigned long long c = p.c[g] > p.mn[g] ? p.c[g] : p.mn[g];
+            const unsigned long long m = round_min(p, g);
+            const unsigned long long c = p.c[g] > m ? p.c[g] : m;
             const int left = *(volatile int32_t*)(p.left + g);
             if (left > 0 && c + 1 >= (unsigned long long)left) {
                 core[v] = (C)c;
@@ -275,8 +305,10 @@ __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict_
     for (int i = threadIdx.x; i < kRcCount; i += blockDim.x) st->rc[i] = 0;
     // every graph: c = max(c, this round's minimum); minima reset
     for (int64_t q = threadIdx.x; q < ngraphs; q += blockDim.x) {
-        if (p.mn[q] != ~0ull && p.mn[q] > p.c[q]) p.c[q] = p.mn[q];
+        const unsigned long long m = round_min(p, (int)q);
+        if (m != ~0ull && m > p.c[q]) p.c[q] = m;
         p.mn[q] = ~0ull;
+        p.mr[q] = ~0ull;
         p.mu[q] = ~0ull;
     }
     if (threadIdx.x == 0) {
@@ -359,6 +391,7 @@ PeelState peel_state(const Graph& g) {
     PeelState p;
     p.c = g.pc;
     p.mn = g.pmn;
+    p.mr = g.pmr;
     p.mu = g.pmu;
     p.left = g.pleft;
     p.gid = g.gid;
@@ -406,6 +439,8 @@ int start_peel(Graph& g, bool sampled, cudaStream_t s) {
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.state->rc, 0, sizeof(int) * kRcCount, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(&g.state->nQ, 0, sizeof(int), s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmu, 0xff, sizeof(unsigned long long) * peel_graphs(g), s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmn, 0xff, sizeof(unsigned long long) * peel_graphs(g), s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmr, 0xff, sizeof(unsigned long long) * peel_graphs(g), s));
     return KH_OK;
 }
 
@@ -469,14 +504,15 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
         prof_end(g, kProfPeel, s);
         return refresh_and_finish(g, sampled, s);
     }
-    // U = min of the upper bounds; refine stale nodes with lb <= max(c, U)
+    // U = min of the upper bounds (and of the fresh values); refine stale
+    // nodes with lb <= max(c, U); the refine folds its results into mr
     prof_begin(g, kProfPeel, s);
     if (sampled)
-        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
-                                                                      g.pmu, g.gid);
+        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(
+            g.alive, g.fresh, g.d64, g.n, g.state, g.pmu, g.pmn, g.gid);
     else
-        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state, g.pmu,
-                                                           g.gid);
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.d32, g.n, g.state,
+                                                           g.pmu, g.pmn, g.gid);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     rc = refine(g, sampled, s);
@@ -484,17 +520,13 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     prof_begin(g, kProfPeel, s);
     const PeelState ps = peel_state(g);
     if (sampled) {
-        k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
-                                                                      g.pmn, g.gid);
         k_select<unsigned long long, unsigned long long><<<grid, kPeelThreads, 0, s>>>(
             g.alive, g.d64, g.n, g.state, ps, g.core64, g.round_of, g.listR, g.seen);
-        count_launch(g, 2);
+        count_launch(g, 1);
     } else {
-        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state, g.pmn,
-                                                           g.gid);
         k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
             g.alive, g.d32, g.n, g.state, ps, g.core32, g.round_of, g.listR, g.seen);
-        count_launch(g, 2);
+        count_launch(g, 1);
         if (!g.gid)  // the early stop of Sec. 5
             k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, ps, g.core32,
                                                                  g.round_of);
@@ -600,6 +632,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     const size_t pbytes = sizeof(unsigned long long) * (size_t)peel_graphs(g);
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pc, 0, pbytes, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmn, 0xff, pbytes, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmr, 0xff, pbytes, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.pmu, 0xff, pbytes, s));
     if (g.gid) {
         // alive nodes per graph start at the graph sizes

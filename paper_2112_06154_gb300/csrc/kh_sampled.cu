@@ -77,6 +77,7 @@ struct LevelArgs {
     unsigned long long* lvl_changed;
     unsigned long long* stopped;
     int8_t* rho;  // tracked passes: top rank of each changed list's changes
+    unsigned long long* min_done;  // refine: per-graph minimum of the completed values
 };
 
 constexpr int kL1Heavy = 512;
@@ -212,7 +213,9 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
         if (lane == 0) my_bytes += level1_bytes(e - b, Skap, nl.last);
         if (nl.last) {
             if (lane == 0) {
-                a.est[v] = estimate_of(Skap, kappa, rv, nl.M);
+                const unsigned long long e = estimate_of(Skap, kappa, rv, nl.M);
+                a.est[v] = e;
+                if (a.min_done) atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), e);
                 record_change(a, nl, v, Skap, kappa);
                 atomicAdd(a.updates, 1ull);
             }
@@ -296,7 +299,9 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
         const int kappa = s_kappa, Skap = s_S;
         if (nl.last) {
             if (tid == 0) {
-                a.est[v] = estimate_of(Skap, kappa, rv, nl.M);
+                const unsigned long long e = estimate_of(Skap, kappa, rv, nl.M);
+                a.est[v] = e;
+                if (a.min_done) atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), e);
                 record_change(a, nl, v, Skap, kappa);
                 atomicAdd(a.updates, 1ull);
                 atomicAdd(a.bytes, level1_bytes(e - b, Skap, 1));
@@ -670,7 +675,9 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         if (tid == 0) my_bytes += 8ull + 10ull * (unsigned long long)deg + 5ull;
         if (nl.last) {
             if (tid == 0) {
-                a.est[v] = estimate_of(S, kappa, rv, nl.M);
+                const unsigned long long e = estimate_of(S, kappa, rv, nl.M);
+                a.est[v] = e;
+                if (a.min_done) atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), e);
                 record_change(a, nl, v, S, kappa);
                 atomicAdd(a.updates, 1ull);
                 my_bytes += 8;
@@ -909,6 +916,7 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.lb = g.lb64;
     a.fresh = g.fresh;
     a.rho = g.rho;
+    a.min_done = (round_mode == 2 && !g.dense) ? g.pmr : nullptr;
     a.lvl_work = g.state->lvl_work;
     a.lvl_changed = g.state->lvl_changed;
     a.stopped = &g.state->stopped;
