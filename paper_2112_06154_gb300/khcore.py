@@ -181,14 +181,29 @@ def kh_last_error(ctx: Ctx) -> str:
     return ctx.error()
 
 
+def _csr_arrays(rowptr, col):
+    """Typed, contiguous CSR arrays whose sizes agree: the C ABI takes rowptr[n]
+    as the length of col, so a shorter col would be read past its end."""
+    if _is_torch(rowptr) or _is_torch(col):
+        import torch
+        if not (_is_torch(rowptr) and _is_torch(col)):
+            raise KhError(KH_EINVAL, "rowptr and col must both be torch tensors or both numpy")
+        if rowptr.dtype != torch.int64 or col.dtype != torch.int32:
+            raise KhError(KH_EINVAL, "rowptr must be int64 and col int32")
+        rowptr, col = rowptr.contiguous(), col.contiguous()
+        if rowptr.numel() < 1 or int(rowptr[-1].item()) != col.numel():
+            raise KhError(KH_EGRAPH, "rowptr[-1] must equal the length of col")
+        return rowptr, col
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if rowptr.ndim != 1 or rowptr.size < 1 or int(rowptr[-1]) != col.size:
+        raise KhError(KH_EGRAPH, "rowptr[-1] must equal the length of col")
+    return rowptr, col
+
+
 def kh_graph_load_csr(ctx: Ctx, rowptr, col) -> Graph:
     """rowptr int64[n+1], col int32[nnz]: both numpy (host) or both torch CUDA tensors."""
-    if _is_torch(rowptr):
-        import torch
-        assert rowptr.dtype == torch.int64 and col.dtype == torch.int32
-    else:
-        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
-        col = np.ascontiguousarray(col, dtype=np.int32)
+    rowptr, col = _csr_arrays(rowptr, col)
     n = int(rowptr.shape[0]) - 1
     pr, dev = _ptr(rowptr)
     pc, _ = _ptr(col)
@@ -367,12 +382,11 @@ def kh_graph_load_batch(ctx: Ctx, vtx_off, rowptr, col, h_per_graph=None) -> Gra
     int32[g] on the host; rowptr/col numpy (host) or torch CUDA tensors."""
     vtx_off = np.ascontiguousarray(vtx_off, dtype=np.int64)
     hpg = None if h_per_graph is None else np.ascontiguousarray(h_per_graph, dtype=np.int32)
-    if _is_torch(rowptr):
-        import torch
-        assert rowptr.dtype == torch.int64 and col.dtype == torch.int32
-    else:
-        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
-        col = np.ascontiguousarray(col, dtype=np.int32)
+    rowptr, col = _csr_arrays(rowptr, col)
+    if vtx_off.size < 1 or int(vtx_off[-1]) != int(rowptr.shape[0]) - 1:
+        raise KhError(KH_EINVAL, "vtx_off[-1] must equal the number of nodes")
+    if hpg is not None and hpg.size != vtx_off.size - 1:
+        raise KhError(KH_EINVAL, "h_per_graph needs one entry per graph")
     pr, dev = _ptr(rowptr)
     pc, _ = _ptr(col)
     h = ctypes.c_void_p()

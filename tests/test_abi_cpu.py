@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2112_06154_gb300 import build as B
@@ -54,3 +55,15 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert K.load().kh_peel_stats(None, None, None, None) == K.KH_EINVAL
     assert K.load().kh_prof_trace(None, 0, None, 0, None) == K.KH_EINVAL
     assert K.load().kh_debug_fail_alloc(None, 1) == K.KH_EINVAL
+
+
+def test_binding_rejects_mismatched_csr_before_the_library():
+    # the C ABI reads rowptr[n] column ids; the binding checks the arrays agree
+    rowptr = np.array([0, 2, 3], np.int64)
+    with pytest.raises(K.KhError):
+        K.kh_graph_load_csr(None, rowptr, np.array([1], np.int32))
+    with pytest.raises(K.KhError):
+        K.kh_graph_load_batch(None, np.array([0, 5], np.int64), rowptr, np.array([1, 0, 0], np.int32))
+    with pytest.raises(K.KhError):
+        K.kh_graph_load_batch(None, np.array([0, 2], np.int64), rowptr, np.array([1, 0, 0], np.int32),
+                              h_per_graph=np.array([2, 3], np.int32))
