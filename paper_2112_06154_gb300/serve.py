@@ -95,6 +95,8 @@ class KhServer:
     """slots: concurrent requests on the GPU; mem_budget: device bytes they may hold."""
 
     def __init__(self, runner_factory, slots: int = 4, mem_budget: int = 64 << 30):
+        if slots < 1 or mem_budget < 1:
+            raise ValueError("a server needs at least one slot and a positive memory budget")
         self.slots = slots
         self.mem_budget = mem_budget
         self.mem_in_use = 0

@@ -146,3 +146,10 @@ def test_concurrent_clients():
     for k in range(8):
         assert results[k] == [10 + k] * 10
     assert len(srv.done) == 80 and srv.mem_in_use == 0 and srv.peak_running <= 3
+
+
+def test_server_refuses_a_configuration_that_cannot_serve():
+    with pytest.raises(ValueError):
+        S.KhServer(fake_factory([]), slots=0)
+    with pytest.raises(ValueError):
+        S.KhServer(fake_factory([]), slots=2, mem_budget=0)
