@@ -191,7 +191,10 @@ int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps) {
 static int64_t budget_M(int64_t n, double eps, double delta) {
     // Eq. (buffer): M = 1 + 4(2 + eps)/eps^2 (C + log 8), C = log(2n/delta)
     const double C = std::log(2.0 * (double)n / delta);
-    return (int64_t)std::floor(1.0 + 4.0 * (2.0 + eps) / (eps * eps) * (C + std::log(8.0)));
+    const double m = std::floor(1.0 + 4.0 * (2.0 + eps) / (eps * eps) * (C + std::log(8.0)));
+    // a tiny eps overflows the double range: saturate (the caller's range check rejects it)
+    if (!(m < 9.0e18)) return INT64_MAX;
+    return (int64_t)m;
 }
 
 static void free_graph_arrays(Graph& g) {
