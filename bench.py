@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "(k,h)-core decomposition: h-degree updates/s"
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth (context beside the measured peak)
 UNIT = "updates/s"
 N_NODES, AVG_DEG, GAMMA, MAX_DEG, GRAPH_SEED = 200_000, 20, 2.5, 5000, 1002
 HS = (2, 3)
@@ -301,6 +302,8 @@ def run_ours(args):
     traffic = profile_traffic(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "nominal_peak": NOMINAL_HBM_GBS,
+                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "traffic": traffic,
                 "alg_bytes_per_launch": d["alg_bytes"] / max(d["launches"], 1),
                 "avg_launch_ms": d["ms"] / max(d["launches"], 1),
