@@ -70,6 +70,8 @@ def _load():
     lib.kho_hdegree_some.restype = ctypes.c_int
     lib.kho_estimate_def_some.argtypes = [i64, P, P, P, P, i32, i64, P, i64, P, P, P]
     lib.kho_estimate_def_some.restype = ctypes.c_int
+    lib.kho_dp_level.argtypes = [i64, P, P, P, i32, i64, P, P, P, i64, i64, P, P, P, P]
+    lib.kho_dp_level.restype = ctypes.c_int
     lib.kho_dense_curve.argtypes = [i64, P, P, P, i32, i64, i32, P, i32, P, P]
     lib.kho_dense_curve.restype = ctypes.c_int
     _lib = lib
@@ -233,3 +235,35 @@ def dense_curve(rowptr, col, r, h: int, M: int, exact: bool, round_of, rounds: i
     _check(_load().kho_dense_curve(n, _p(rowptr), _p(col), _p(r), h, max(M, 1), 1 if exact else 0,
                                    _p(ro), rounds, _p(total), _p(size)), "dense_curve")
     return total[:rounds], size[:rounds]
+
+
+def dp_level(rowptr, col, r, i: int, M: int, prev=None, v0: int = 0, v1: int = None):
+    """One level of the list recursion (Alg. 2, Prop. 3.1) for nodes v0..v1-1 of
+    the whole graph.  prev = (off int64[n+1], ids int32[], k uint8[n]) holds the
+    level i-1 lists of every node (None for i = 1).  Returns (k uint8, size
+    int32, est uint64, off int64[m+1], ids int32[]) for the m = v1 - v0 nodes,
+    each list sorted by rank descending then id."""
+    rowptr, col, n = _graph(rowptr, col)
+    v1 = n if v1 is None else v1
+    m = v1 - v0
+    r = np.ascontiguousarray(r, dtype=np.uint8)
+    k = np.zeros(max(m, 1), np.uint8)
+    size = np.zeros(max(m, 1), np.int32)
+    est = np.zeros(max(m, 1), np.uint64)
+    slots = np.zeros(max(m, 1) * M, np.int32)
+    if prev is not None:
+        poff = np.ascontiguousarray(prev[0], dtype=np.int64)
+        pids = np.ascontiguousarray(prev[1], dtype=np.int32)
+        pk = np.ascontiguousarray(prev[2], dtype=np.uint8)
+        if pids.size == 0:
+            pids = np.zeros(1, np.int32)
+    else:
+        poff = pids = pk = None
+    _check(_load().kho_dp_level(n, _p(rowptr), _p(col), _p(r), i, M, _p(poff), _p(pids),
+                                _p(pk), v0, v1, _p(k), _p(size), _p(slots), _p(est)), "dp_level")
+    k, size, est = k[:m], size[:m], est[:m]
+    off = np.zeros(m + 1, np.int64)
+    np.cumsum(size, out=off[1:])
+    keep = (np.arange(M)[None, :] < size[:, None]) if m else np.zeros((0, M), bool)
+    ids = slots[:m * M].reshape(m, M)[keep]
+    return k, size, est, off, ids

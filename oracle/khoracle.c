@@ -20,6 +20,8 @@
  *                         (equal to Alg. 1's output, Sec. 4).
  *   kho_estimate_dp       B[v,i], k[v,i] by the naive Compute (Alg. 2) level by
  *                         level (Prop. 3.1), then Estimate (Alg. 1).
+ *   kho_dp_level          the same Compute for one level and a range of nodes,
+ *                         the previous level given as arrays (large graphs).
  *   kho_core_exact        ExactCore (Sec. 2): peel by smallest deg_h.
  *   kho_core_sampled      Core (Alg. 4) with naive Update (Alg. 3).
  *   kho_dense_curve       EstDense (Alg. 7, Sec. 6): along a removal order, the
@@ -475,6 +477,95 @@ int kho_estimate_dp(int64_t n, const int64_t *rowptr, const int32_t *col,
     dp_free(&dp);
     free(alive);
     return rc;
+}
+
+/* One level of the list recursion for a range of nodes of the whole graph
+ * (Prop. 3.1 with the naive Compute of Alg. 2), from the previous level's
+ * lists of every node passed in as arrays, so that a large graph can be done
+ * level by level and range by range.  Level i = 1 takes B[w,0] = {w} and
+ * k[w,0] = 0 (prev_* unused); level i >= 2 reads B[w,i-1] at
+ * prev_ids[prev_off[w] .. prev_off[w+1]) and k[w,i-1] = prev_k[w].
+ * For v = v0 + q, q < v1 - v0:
+ *   T = {v} union the B[w,i-1] of w in A(v), sorted by rank (descending, ties
+ *   by id) without repeats; k = max of the k[w,i-1]; if |T| > M then
+ *   k = max(k, r[t_(M+1)] + 1); B[v,i] = {u in T : r[u] >= k} (at most M
+ *   members, written in T's order to out_ids[q*M ..]);
+ *   out_k[q] = k, out_size[q] = |B[v,i]|, and out_est[q] = Alg. 1 on
+ *   (B[v,i], k): |B[v,i] \ {v}| 2^k, raised to M 2^(k-1) when k > 0. */
+int kho_dp_level(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *r,
+                 int32_t i, int64_t M, const int64_t *prev_off, const int32_t *prev_ids,
+                 const uint8_t *prev_k, int64_t v0, int64_t v1, uint8_t *out_k,
+                 int32_t *out_size, int32_t *out_ids, uint64_t *out_est)
+{
+    (void)n;
+    if (i < 1 || M < 1 || v0 < 0 || v1 < v0)
+        return KHO_EINVAL;
+    int64_t tcap = 1024;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)tcap);
+    if (!t)
+        return KHO_ENOMEM;
+    for (int64_t v = v0; v < v1; v++) {
+        int64_t q = v - v0;
+        int64_t need = 1;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++) {
+            int32_t w = col[e];
+            need += (i == 1) ? 1 : prev_off[w + 1] - prev_off[w];
+        }
+        if (need > tcap) {
+            int32_t *nt = (int32_t *)realloc(t, sizeof(int32_t) * (size_t)need);
+            if (!nt) {
+                free(t);
+                return KHO_ENOMEM;
+            }
+            t = nt;
+            tcap = need;
+        }
+        int64_t len = 0;
+        int k = 0;
+        t[len++] = (int32_t)v;
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++) {
+            int32_t w = col[e];
+            if (i == 1) {
+                t[len++] = w;
+            } else {
+                for (int64_t p = prev_off[w]; p < prev_off[w + 1]; p++)
+                    t[len++] = prev_ids[p];
+                if (prev_k[w] > k)
+                    k = prev_k[w];
+            }
+        }
+        g_sort_r = r;
+        qsort(t, (size_t)len, sizeof(int32_t), cmp_rank_desc_id_asc);
+        int64_t u = 0;
+        for (int64_t p = 0; p < len; p++)
+            if (u == 0 || t[p] != t[u - 1])
+                t[u++] = t[p];
+        len = u;
+        if (len > M) {
+            int kk = r[t[M]] + 1; /* t_(M+1), 1-based */
+            if (kk > k)
+                k = kk;
+        }
+        int32_t size = 0, others = 0;
+        for (int64_t p = 0; p < len; p++)
+            if (r[t[p]] >= k) {
+                out_ids[q * M + size] = t[p];
+                size++;
+                if (t[p] != (int32_t)v)
+                    others++;
+            }
+        uint64_t d = (uint64_t)others << k;
+        if (k > 0) {
+            uint64_t f = (uint64_t)M << (k - 1);
+            if (f > d)
+                d = f;
+        }
+        out_k[q] = (uint8_t)k;
+        out_size[q] = size;
+        out_est[q] = d;
+    }
+    free(t);
+    return KHO_OK;
 }
 
 /* ------------------------------------------------------------------------ */

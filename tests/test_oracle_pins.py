@@ -208,6 +208,32 @@ def test_level_recursion_equals_definition(h, M):
             assert (x == y).all()
 
 
+@pytest.mark.parametrize("h,M", [(1, 5), (2, 3), (3, 16), (4, 7)])
+def test_level_by_level_ranges_equal_definition(h, M):
+    """dp_level chained over levels and cut into node ranges gives Def. 4.1 on
+    the whole ball (est, k, |B|), and each list is the rank filter of the ball
+    at its level, in rank order (Prop. 3.1)."""
+    rp, cl = gg.chung_lu(900, 9, 2.4, 120, 33)
+    n = rp.size - 1
+    r = O.ranks(n, 2)
+    prev = None
+    for i in range(1, h + 1):
+        parts = [O.dp_level(rp, cl, r, i, M, prev, a, min(n, a + 97)) for a in range(0, n, 97)]
+        k = np.concatenate([p[0] for p in parts])
+        size = np.concatenate([p[1] for p in parts])
+        est = np.concatenate([p[2] for p in parts])
+        ids = np.concatenate([p[4] for p in parts])
+        off = np.zeros(n + 1, np.int64)
+        np.cumsum(size, out=off[1:])
+        prev = (off, ids, k)
+        we, wk, ws = O.estimate_def(rp, cl, r, i, M)
+        assert (est == we).all() and (k == wk).all() and (size == ws).all()
+        for v in (0, 17, 450, n - 1):
+            ball = O.hball(rp, cl, v, i)
+            want = sorted((u for u in ball if r[u] >= k[v]), key=lambda u: (-int(r[u]), u))
+            assert list(ids[off[v]:off[v + 1]]) == want
+
+
 def test_level_thresholds_monotone_prop31():
     """k[v,i] >= k[w,i-1] for w adjacent to v, and |B[v,i]| <= M (Prop. 3.1)."""
     rp, cl = gg.chung_lu(2000, 10, 2.3, 400, 4)
