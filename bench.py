@@ -1,21 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the (k,h)-core hot path on one GB300 (or N replicas).
 
-Workload: seeded Chung-Lu power-law graph, n = 200,000, about 2M undirected
-edges, degree exponent 2.5, maximum expected degree 5,000 (graph seed 1002),
-at h = 2 and h = 3, eps = 0.5, delta = 0.05 (M = 719), rank seed 1.
+Default workload (--workload rmat): the R-MAT scale-22 graph (4,194,304
+nodes; 16 * 2^22 edge draws with a = 0.57, b = c = 0.19, d = 0.05,
+symmetrised, deduplicated, self-loops dropped, ids permuted; graph seed 1003),
+eps = 0.5, delta = 0.05 (M = 841), rank seed 1.  One step is one pass of the
+hot path over that graph:
+  ranks; exact h-degrees at h = 2; adaptive estimates (level recursion and
+  Alg. 1) at h = 2, 3 and 4; the sampled (k,3)-core decomposition (Core,
+  Alg. 4, bucket-synchronous).
+--workload chung_lu runs the Chung-Lu n = 200,000 graph (m ~ 2M, exponent
+2.5, maximum expected degree 5,000, graph seed 1002) with, for h = 2 and 3:
+ranks, exact h-degrees, fixed-level counts j = 0..10, the adaptive estimate
+and the sampled core; then the exact (k,2)-core.
 
-One step is one pass of the whole hot path over that graph:
-  for h in (2, 3): ranks; exact h-degrees; fixed-level counts j = 0..10
-                   (sampling probability 1 .. 1/1024); adaptive estimate;
-                   sampled (k,h)-core decomposition (Core, Alg. 4);
-  then the exact (k,2)-core decomposition (ExactCore, with early stop).
-The metric is h-degree updates per second: one update is one (re)computation
-of one alive node's h-degree or of its B[.,h] and estimate (initial passes
-count n each).  ms_per_step is the wall time of that whole decomposition pass.
+The metric is h-degree updates per second: one update is one completed
+(re)computation of one alive node's h-degree, or of its B[., h] and estimate
+(a full-graph pass counts n; a refine that stopped early with only a lower
+bound does not count).  ms_per_step is the device time of one whole pass.
 
 --impl reference times the CPU oracle (single thread) on a bounded sample of
-the same workload: exact h-degrees of all nodes at h = 2 per step.
+the same workload: exact h = 2 degrees and Def. 4.1 estimates at h = 2 of a
+seeded sample of nodes per step.
 """
 from __future__ import annotations
 
@@ -32,13 +38,116 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "(k,h)-core decomposition: h-degree updates/s"
-NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth (context beside the measured peak)
 UNIT = "updates/s"
-N_NODES, AVG_DEG, GAMMA, MAX_DEG, GRAPH_SEED = 200_000, 20, 2.5, 5000, 1002
-HS = (2, 3)
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth (context beside the measured peak)
 EPS, DELTA, RANK_SEED = 0.5, 0.05, 1
 J_LO, J_HI = 0, 10
+E2E_STEPS = 3  # end-to-end steps (graph upload included), capped to keep the run short
+
+# kernel class -> the kernels it brackets (kh_prof_read kinds)
+CLASS_KERNELS = {
+    "bfs": "k_hdeg / k_hdeg2_slice (exact h-degree BFS)",
+    "level1": "k_level1, k_level1_heavy (level-1 lists)",
+    "levelU": "k_levelU (level >= 2 lists, hashed union with trim)",
+    "frontier": "k_mark_nbrs, k_ball_hop, k_stale_*, k_apply_loss",
+    "peel": "k_min_alive, k_collect, k_select, k_finish",
+}
+
+
+class Workload:
+    """A headline workload: its graph, one step through the C ABI, its config."""
+
+    def __init__(self, key):
+        self.key = key
+        if key == "rmat":
+            self.name = "rmat_scale22_ef16_h2exact_h234estimate_k3core"
+            self.metric = "(k,h)-core decomposition on R-MAT scale 22: h-degree updates/s"
+            self.graph_desc = ("R-MAT scale 22, edge factor 16, a/b/c/d = .57/.19/.19/.05, "
+                               "symmetrised, deduplicated, ids permuted (synthetic stand-in for "
+                               "the paper's social and web graphs)")
+            self.graph_seed = 1003
+            self.step_desc = ("ranks; exact h-degrees at h=2; adaptive estimate at h=2,3,4; "
+                              "sampled (k,3)-core")
+        else:
+            self.name = "chung_lu_n200k_m2M_gamma2.5_h2_h3"
+            self.metric = "(k,h)-core decomposition on Chung-Lu n=200k: h-degree updates/s"
+            self.graph_desc = "Chung-Lu power law (synthetic stand-in for the paper's social graphs)"
+            self.graph_seed = 1002
+            self.step_desc = ("per h in (2,3): ranks, exact h-degrees, fixed-level counts j=0..10, "
+                              "adaptive estimate, sampled core; plus exact (k,2)-core")
+
+    def make_graph(self):
+        from paper_2112_06154_gb300 import graphgen as gg
+        if self.key == "rmat":
+            return gg.rmat(22, 16, 0.57, 0.19, 0.19, self.graph_seed)
+        return gg.chung_lu(200_000, 20, 2.5, 5000, self.graph_seed)
+
+    def config(self, rp, cl, M):
+        deg = np.diff(rp)
+        return {
+            "workload": self.name, "graph": self.graph_desc,
+            "n": int(rp.size - 1), "m": int(cl.size // 2), "max_deg": int(deg.max()),
+            "isolated": int((deg == 0).sum()), "eps": EPS, "delta": DELTA, "M": int(M),
+            "rank_seed": RANK_SEED, "graph_seed": self.graph_seed, "step": self.step_desc,
+            "l2": "inputs larger than L2 (col array %d MB) and L2 flushed (512 MB write) "
+                  "between timed steps" % (cl.nbytes >> 20),
+        }
+
+    def step(self, K, graph, n, out=None):
+        """One pass; out=None: host outputs (e2e).  Returns completed updates."""
+        dev = out is not None
+        o = (lambda k: out[k]) if dev else (lambda k: None)
+        updates = 0
+        if self.key == "rmat":
+            K.kh_set_h(graph, 2)
+            K.kh_ranks(graph, o("r"))
+            K.kh_hdegree_exact(graph, o("deg"))
+            updates += n
+            for h in (2, 3, 4):
+                K.kh_set_h(graph, h)
+                if dev:
+                    K.kh_estimate(graph, out["est%d" % h], out["lvl%d" % h], out["bs%d" % h])
+                else:
+                    K.kh_estimate(graph)
+                updates += n
+            K.kh_set_h(graph, 3)
+            K.kh_core_sampled(graph, o("cs"))
+            updates += K.kh_peel_info(graph, False)[2]
+            return updates
+        for h in (2, 3):
+            K.kh_set_h(graph, h)
+            K.kh_ranks(graph, o("r"))
+            K.kh_hdegree_exact(graph, o("deg"))
+            K.kh_sampled_counts(graph, J_LO, J_HI, o("cnt"))
+            if dev:
+                K.kh_estimate(graph, out["est%d" % h], out["lvl%d" % h], out["bs%d" % h])
+            else:
+                K.kh_estimate(graph)
+            K.kh_core_sampled(graph, o("cs"))
+            updates += 3 * n + K.kh_peel_info(graph, False)[2]
+        K.kh_set_h(graph, 2)
+        K.kh_core_exact(graph, o("ce"))
+        updates += K.kh_peel_info(graph, False)[2]
+        return updates
+
+    def device_outputs(self, n):
+        import torch
+        td = lambda *shape, dt: torch.empty(*shape, dtype=dt, device="cuda")
+        out = {"r": td(n, dt=torch.uint8), "deg": td(n, dt=torch.int32),
+               "cs": td(n, dt=torch.int64), "ce": td(n, dt=torch.int32),
+               "cnt": td(n, J_HI - J_LO + 1, dt=torch.int32)}
+        for h in (2, 3, 4):
+            out["est%d" % h] = td(n, dt=torch.int64)
+            out["lvl%d" % h] = td(n, dt=torch.uint8)
+            out["bs%d" % h] = td(n, dt=torch.int32)
+        return out
+
+    def d2h_bytes(self, n):
+        if self.key == "rmat":
+            # ranks, degrees, 3 estimates (est, level, |B|), sampled core
+            return n * (1 + 4 + 3 * (8 + 1 + 4) + 8)
+        nj = J_HI - J_LO + 1
+        return 2 * n * (1 + 4 + 4 * nj + 8 + 1 + 4 + 8) + 4 * n
 
 
 def parse():
@@ -49,13 +158,15 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "sampled2",
-                                    "sampled3", "exact2"],
-                   help="run one operation of the step once (a target for profilers) and exit")
-    p.add_argument("--workload", choices=["chung_lu", "batch", "serve", "rmat", "dense", "sweep"],
-                   default="chung_lu",
-                   help="batch: 4096 preferential-attachment graphs, batched vs one graph per call; "
-                        "serve: a Poisson request stream through the continuous-batching server")
+    p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "est4",
+                                    "sampled2", "sampled3", "sampled4", "exact2"],
+                   help="run one operation once on the workload's graph (a target for profilers)")
+    p.add_argument("--workload", choices=["rmat", "chung_lu", "rmat_ops", "batch", "serve",
+                                          "dense", "sweep"],
+                   default="rmat",
+                   help="rmat (default) / chung_lu: headline step; rmat_ops: single operations on "
+                        "R-MAT 22; batch: 4096 preferential-attachment graphs, batched vs one graph "
+                        "per call; serve: a Poisson request stream through the server")
     p.add_argument("--requests", type=int, default=300)
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--pool", type=int, default=24)
@@ -71,24 +182,6 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
-
-
-def make_graph():
-    from paper_2112_06154_gb300 import graphgen as gg
-    return gg.chung_lu(N_NODES, AVG_DEG, GAMMA, MAX_DEG, GRAPH_SEED)
-
-
-def config(rp, cl, M):
-    return {
-        "workload": "chung_lu_n200k_m2M_gamma2.5_h2_h3",
-        "graph": "Chung-Lu power law (synthetic stand-in for the paper's social graphs)",
-        "n": int(rp.size - 1), "m": int(cl.size // 2), "max_deg": int(np.diff(rp).max()),
-        "h": list(HS), "eps": EPS, "delta": DELTA, "M": int(M), "rank_seed": RANK_SEED,
-        "graph_seed": GRAPH_SEED, "fixed_levels": [J_LO, J_HI],
-        "step": "per h: ranks, exact h-degrees, fixed-level counts, adaptive estimate, "
-                "sampled core; plus exact (k,2)-core",
-        "l2": "flushed (512 MB write) between timed steps",
-    }
 
 
 class Clocks:
@@ -120,7 +213,7 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.splitlines():
             f = [x.strip() for x in line.split(",")]
@@ -129,6 +222,7 @@ class Clocks:
             try:
                 sm.append(float(f[0]))
                 smax.append(float(f[1]))
+                power.append(float(f[2]))
             except ValueError:
                 continue
             for nm, val in zip(names, f[4:8]):
@@ -136,6 +230,7 @@ class Clocks:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
@@ -147,15 +242,18 @@ def load_peak():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kind_name):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary, if any."""
+def profile_traffic(workload, kind_name):
+    """DRAM bytes per launch of a kernel class on a workload, from the committed
+    ncu summary (None when the class is not listed there)."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     try:
         with open(path) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) >= 2 and parts[0] == kind_name and not line.startswith("#"):
-                    return float(parts[1])
+                if line.startswith("#") or len(parts) < 3:
+                    continue
+                if parts[0] == workload and parts[1] == kind_name:
+                    return float(parts[2])
     except OSError:
         pass
     return None
@@ -181,6 +279,7 @@ def run_ours(args):
     import torch
     from paper_2112_06154_gb300 import khcore as K
 
+    wl = Workload(args.workload)
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -190,46 +289,15 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     K.load(build_if_missing=True)
-    rp, cl = make_graph()
+    rp, cl = wl.make_graph()
     n = rp.size - 1
     stream = torch.cuda.Stream()
     ctx = K.kh_ctx_create(dev, stream)
     G = K.kh_graph_load_csr(ctx, rp, cl)
     K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
     M = K.kh_get_M(G)
-    nj = J_HI - J_LO + 1
-    td = lambda *shape, dt: torch.empty(*shape, dtype=dt, device="cuda")
-    out = {
-        "r": td(n, dt=torch.uint8), "deg": td(n, dt=torch.int32), "cnt": td(n, nj, dt=torch.int32),
-        "est": td(n, dt=torch.int64), "lvl": td(n, dt=torch.uint8), "bs": td(n, dt=torch.int32),
-        "cs": td(n, dt=torch.int64), "ce": td(n, dt=torch.int32),
-    }
+    out = wl.device_outputs(n)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-
-    def step(graph, host):
-        updates = 0
-        for h in HS:
-            K.kh_set_h(graph, h)
-            if host:
-                K.kh_ranks(graph)
-                K.kh_hdegree_exact(graph)
-                K.kh_sampled_counts(graph, J_LO, J_HI)
-                K.kh_estimate(graph)
-                K.kh_core_sampled(graph)
-            else:
-                K.kh_ranks(graph, out["r"])
-                K.kh_hdegree_exact(graph, out["deg"])
-                K.kh_sampled_counts(graph, J_LO, J_HI, out["cnt"])
-                K.kh_estimate(graph, out["est"], out["lvl"], out["bs"])
-                K.kh_core_sampled(graph, out["cs"])
-            updates += 3 * n + K.kh_peel_info(graph, False)[2]
-        K.kh_set_h(graph, 2)
-        if host:
-            K.kh_core_exact(graph)
-        else:
-            K.kh_core_exact(graph, out["ce"])
-        updates += K.kh_peel_info(graph, False)[2]
-        return updates
 
     def barrier():
         if world > 1:
@@ -238,7 +306,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step(G, False)
+        wl.step(K, G, n, out)
         K.kh_sync(G)
     clocks = Clocks(dev if world == 1 else local)
     total_ms = 0.0
@@ -252,44 +320,48 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        total_updates += step(G, False)
+        total_updates += wl.step(K, G, n, out)
         e1.record(stream)
         barrier()
         total_ms += e0.elapsed_time(e1)
     clk = clocks.stop()
     launches = K.kh_launch_count(G) - launches0
 
-    # e2e: the same steps through the C ABI with host buffers, graph upload included
+    # e2e: the same step through the C ABI with host buffers: the graph upload
+    # from pinned host memory (and its validation), every output read back
     e2e = None
     if not args.no_e2e:
+        prp = torch.from_numpy(rp).pin_memory()
+        pcl = torch.from_numpy(cl).pin_memory()
         h2d = rp.nbytes + cl.nbytes
-        d2h = 0
-        for h in HS:
-            d2h += n * (1 + 4 + 4 * nj + 8 + 1 + 4 + 8)
-        d2h += 4 * n
-        Gw = K.kh_graph_load_csr(ctx, rp, cl)   # warm-up
+        d2h = wl.d2h_bytes(n)
+        Gw = K.kh_graph_load_csr(ctx, prp, pcl)  # warm-up
         K.kh_set_sampling(Gw, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
-        step(Gw, True)
+        wl.step(K, Gw, n)
         Gw.close()
         barrier()
         t_e2e = 0.0
         upd_e2e = 0
-        for _ in range(args.steps):
+        e2e_steps = max(1, min(args.steps, E2E_STEPS))
+        for _ in range(e2e_steps):
             barrier()
             t0 = time.perf_counter()
-            Ge = K.kh_graph_load_csr(ctx, rp, cl)
+            Ge = K.kh_graph_load_csr(ctx, prp, pcl)
             K.kh_set_sampling(Ge, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
-            upd_e2e += step(Ge, True)
+            upd_e2e += wl.step(K, Ge, n)
             K.kh_sync(Ge)
             t_e2e += time.perf_counter() - t0
             Ge.close()
         e2e = {"value": upd_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps,
+               "ms_per_step": 1e3 * t_e2e / e2e_steps,
+               "timing": "host wall clock around graph upload (pinned host arrays), the step "
+                         "with host outputs, and a stream sync"}
 
-    # roofline: one extra profiled step (kernel classes timed with CUDA events
-    # on the library's stream, algorithmic bytes counted on the device)
+    # roofline: one extra profiled step (kernel classes bracketed with CUDA
+    # events on the library's stream, algorithmic bytes counted on the device)
     K.kh_prof_enable(G, True)
-    step(G, False)
+    wl.step(K, G, n, out)
     prof = {}
     for kind in range(K.KH_PROF_KINDS):
         ms, nl, byts = K.kh_prof_read(G, kind)
@@ -299,8 +371,9 @@ def run_ours(args):
     d = prof[dom]
     peak, peak_src = load_peak()
     achieved = (d["alg_bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
-    traffic = profile_traffic(dom)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak,
+    traffic = profile_traffic(wl.name, dom)
+    roofline = {"bound": "hbm", "kernel": CLASS_KERNELS.get(dom, dom), "class": dom,
+                "achieved": round(achieved, 2), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "nominal_peak": NOMINAL_HBM_GBS,
                 "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
@@ -311,6 +384,7 @@ def run_ours(args):
                 "timing": "kernel-class CUDA events on the library stream, one profiled step "
                           "after the timed region",
                 "classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                                "alg_GB": round(v["alg_bytes"] / 1e9, 3),
                                 "GBps": round(v["alg_bytes"] / 1e6 / v["ms"], 1) if v["ms"] else 0}
                             for k, v in prof.items()}}
 
@@ -318,15 +392,15 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(rp, cl, M)
+        cpu = cpu_baseline(wl, rp, cl, M, samples=4000)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": updates_all / (total_ms_max / 1e3), "unit": UNIT,
+            "metric": wl.metric, "value": updates_all / (total_ms_max / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic (seeded Chung-Lu graph; no dataset)",
-            "config": config(rp, cl, M), "roofline": roofline, "cpu_baseline": cpu,
+            "data": "synthetic (seeded generator; no dataset)",
+            "config": wl.config(rp, cl, M), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "updates_per_step": total_updates / args.steps,
         }
@@ -340,58 +414,68 @@ def run_ours(args):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def cpu_baseline(rp, cl, M):
-    """The oracle, single-threaded: exact h-degrees (h=2) and the adaptive
-    estimate through the level recursion (h=2) of every node of the graph."""
+def oracle_sample(wl, rp, cl, M, count, seed):
+    """The oracle on `count` seeded sample nodes of the workload's graph:
+    exact h-degrees at h = 2 and the Def. 4.1 estimate at h = 2.  Returns
+    (updates, seconds)."""
     import oracle as O
     n = rp.size - 1
+    rng = np.random.default_rng(seed)
+    vs = np.sort(rng.choice(n, size=min(count, n), replace=False)).astype(np.int32)
     r = O.ranks(n, RANK_SEED)
     t0 = time.perf_counter()
-    O.hdegree_exact(rp, cl, 2)
-    O.estimate_dp(rp, cl, r, 2, M)
-    dt = time.perf_counter() - t0
-    return {"value": 2 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"exact h-degrees + level-recursion estimate, h=2, all {n} nodes "
-                      f"of the same graph ({dt:.1f} s)"}
+    O.hdegree_some(rp, cl, 2, vs)
+    O.estimate_def_some(rp, cl, r, 2, M, vs)
+    return 2 * vs.size, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, rp, cl, M, samples):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    upd, dt = oracle_sample(wl, rp, cl, M, samples, 7)
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"exact h-degrees and Def. 4.1 estimates at h=2 of {samples} seeded sample "
+                      f"nodes of the same graph ({dt:.1f} s, single thread)"}
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
+    wl = Workload(args.workload if args.workload in ("rmat", "chung_lu") else "rmat")
     import oracle as O
-    rp, cl = make_graph()
+    rp, cl = wl.make_graph()
     n = rp.size - 1
     M = O.budget_M(n, EPS, DELTA)
-    for _ in range(args.warmup):
-        O.hdegree_some(rp, cl, 2, np.arange(0, n, 50))
+    per_step = 400
+    for i in range(args.warmup):
+        oracle_sample(wl, rp, cl, M, 50, 100 + i)
     t = 0.0
     upd = 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.hdegree_exact(rp, cl, 2)
-        t += time.perf_counter() - t0
-        upd += n
+    for i in range(args.steps):
+        u, dt = oracle_sample(wl, rp, cl, M, per_step, 1000 + i)
+        t += dt
+        upd += u
     value = upd / t
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "impl": "reference", "metric": wl.metric, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic (seeded Chung-Lu graph; no dataset)", "config": config(rp, cl, M),
+        "data": "synthetic (seeded generator; no dataset)", "config": wl.config(rp, cl, M),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"exact h-degrees, h=2, all {n} nodes per step "
-                                   "(single-threaded CPU oracle)"},
+                         "sample": f"per step: exact h-degrees and Def. 4.1 estimates at h=2 of "
+                                   f"{per_step} seeded sample nodes (single-threaded CPU oracle)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_op(args):
-    """One operation of the step on the same workload, once, for ncu."""
+    """One operation on the headline workload's graph, once (a target for ncu)."""
     import torch
     from paper_2112_06154_gb300 import khcore as K
     K.load(build_if_missing=True)
-    rp, cl = make_graph()
+    wl = Workload(args.workload if args.workload in ("rmat", "chung_lu") else "rmat")
+    rp, cl = wl.make_graph()
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rp, cl)
     K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
@@ -408,7 +492,7 @@ def run_op(args):
     ctx.close()
 
 
-def run_rmat(args):
+def run_rmat_ops(args):
     """R-MAT scale 22 (a=.57, b=c=.19, 16 edges per node generated, symmetrised,
     deduplicated): exact h-degrees at h=2, adaptive estimates and sampled
     (k,h)-cores at h=2,3,4, each timed once after a warm-up load."""
@@ -423,7 +507,7 @@ def run_rmat(args):
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rowptr, col)
     K.kh_set_sampling(G, seed=1)
-    out = {"workload": "rmat_scale22", "impl": "ours", "graph": stats, "M": K.kh_get_M(G),
+    out = {"workload": "rmat_scale22_ops", "impl": "ours", "graph": stats, "M": K.kh_get_M(G),
            "gen_s": gen_s, "unit": "s", "higher_is_better": False}
 
     def timed(fn):
@@ -463,7 +547,7 @@ def run_dense(args):
     import torch
     from paper_2112_06154_gb300 import khcore as K
     K.load()
-    rowptr, col = make_graph()
+    rowptr, col = Workload("chung_lu").make_graph()
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rowptr, col)
     out = {"workload": "estdense_chung_lu_n200k", "impl": "ours", "unit": "s",
@@ -517,7 +601,7 @@ def run_sweep(args):
 
     out = {"workload": "eps_sweep_and_sbm", "impl": "ours", "unit": "s", "higher_is_better": False,
            "eps_sweep": [], "sbm": []}
-    cases = [("chung_lu_n200k", make_graph(), 2, (0.5, 0.35, 0.25)),
+    cases = [("chung_lu_n200k", Workload("chung_lu").make_graph(), 2, (0.5, 0.35, 0.25)),
              ("chung_lu_n20k", gg.chung_lu(20000, 20, 2.5, 1000, 1102), 3,
               (0.5, 0.4, 0.3, 0.2, 0.15))]
     for name, (rowptr, col), h, eps_list in cases:
@@ -707,8 +791,8 @@ def main():
         run_serve(args)
     elif args.workload == "batch" and args.impl == "ours":
         run_batch(args)
-    elif args.workload == "rmat" and args.impl == "ours":
-        run_rmat(args)
+    elif args.workload == "rmat_ops" and args.impl == "ours":
+        run_rmat_ops(args)
     elif args.workload == "dense" and args.impl == "ours":
         run_dense(args)
     elif args.workload == "sweep" and args.impl == "ours":

@@ -149,7 +149,9 @@ int kh_core_sampled(kh_graph *g, uint64_t *core, uint32_t flags);
 
 /* Statistics of the last kh_core_* call: round_of[v] (int32[n], may be NULL)
  * is the peeling round that removed v; *rounds the number of rounds;
- * *updates the number of node (re)computations including the initial pass.
+ * *updates the number of completed node (re)computations of d, including the
+ * initial pass and the exact decrements of the loss propagation (refines that
+ * stopped early with a lower bound only are counted by kh_peel_stats).
  * Host pointers only. */
 int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updates);
 
@@ -228,6 +230,30 @@ int kh_launch_count(kh_graph *g, int64_t *launches);
  * different streams, or from different threads) race: serialise them. */
 int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, int32_t h,
                              int32_t *deg, void *cuda_stream);
+
+/* Layout of the whole-graph exact h-degree pass at h = 2 (kh_hdegree_exact,
+ * kh_sampled_counts; no counterpart in the paper: the schedule, not the
+ * result).  KH_VAR_CTA: one CTA per source with a visited bitmap of all n
+ * nodes in shared memory (only while n <= 819200); KH_VAR_SLICED: (source,
+ * slice) work items, the id range cut into `slices` ranges whose visited
+ * bitmap fits in shared memory, `threads` per CTA (128, 256, 512 or 1024).
+ * KH_VAR_AUTO (default): the library's autotuner times the candidate layouts
+ * on a sample of the graph's sources at the first such call and keeps the
+ * fastest; with the environment variable KH_TUNE_FILE naming a text file, the
+ * choice is also recorded there per graph shape class (device SM count, log2
+ * n, log2 nnz, log2 of max degree over mean degree) and reused by later
+ * processes.  Every layout returns the same degrees.  kh_set_variant forces
+ * a layout (KH_EINVAL for an unknown op or variant, KH_VAR_CTA with n too
+ * large, or slices outside [the shared-memory minimum, min(1024, n)]);
+ * kh_get_variant returns the layout in force, tuning first if needed, and the
+ * sample time in ms it was chosen with (0 when forced or read from a file). */
+#define KH_OP_HDEG2 0
+#define KH_VAR_AUTO 0
+#define KH_VAR_CTA 1
+#define KH_VAR_SLICED 2
+int kh_set_variant(kh_graph *g, int32_t op, int32_t variant, int32_t slices, int32_t threads);
+int kh_get_variant(kh_graph *g, int32_t op, int32_t *variant, int32_t *slices, int32_t *threads,
+                   double *tuned_ms);
 
 /* Wait for all work enqueued on the graph's context stream. */
 int kh_sync(kh_graph *g);

@@ -351,11 +351,12 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
                 a.fresh[v] = 0;
                 atomicAdd(a.stopped, 1ull);
             } else {
+                // a completed ball is one h-degree update; a stopped one is not
                 a.deg[v] = s_count;
                 if (a.min_done)
                     atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), (unsigned long long)s_count);
+                atomicAdd(a.updates, 1ull);
             }
-            atomicAdd(a.updates, 1ull);
             my_bytes += 4ull + (RANKS ? 4ull * (unsigned long long)a.nj : 0ull);
         }
         if (RANKS && tid < a.nj) {

@@ -660,8 +660,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             if (tid == 0) {
                 a.lb[v] = s_part;
                 a.fresh[v] = 0;
-                atomicAdd(a.updates, 1ull);
-                atomicAdd(a.stopped, 1ull);
+                atomicAdd(a.stopped, 1ull);  // a lower bound only: not an update
                 my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
             }
             __syncthreads();

@@ -38,7 +38,8 @@ def test_sampled_peel_stats(ctx, h):
         assert (chg <= ref).all()
         assert (ref[1:h] > 0).all() and (chg[1:h] > 0).all()
         assert ref[h:].sum() == 0
-        assert 0 <= stopped <= updates
+        # early-stopped refines leave a lower bound only: counted apart from updates
+        assert stopped >= 0 and updates > 0
         ms, launches, _ = K.kh_prof_read(G, K.KH_PROF_LEVELU)
         trace = K.kh_prof_trace(G, K.KH_PROF_LEVELU)
         assert trace.size == launches > 0
@@ -65,7 +66,7 @@ def test_exact_peel_stops_early(ctx):
         _, _, updates = K.kh_peel_info(G, False)
         ref, chg, stopped = K.kh_peel_stats(G)
         assert ref.sum() == 0 and chg.sum() == 0
-        assert 0 < stopped <= updates
+        assert stopped > 0 and updates > 0
         want, _, _ = O.core_exact(rowptr, col, 2)
         assert np.array_equal(core, want)
     finally:
