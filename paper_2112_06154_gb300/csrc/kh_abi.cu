@@ -46,6 +46,10 @@ static int dalloc(kh_ctx* ctx, T** p, size_t count, const char* what) {
     return KH_OK;
 }
 
+int alloc_bytes(kh_ctx* ctx, void** p, size_t bytes, const char* what) {
+    return dalloc(ctx, reinterpret_cast<uint8_t**>(p), bytes, what);
+}
+
 template <typename T>
 static void dfree(T** p) {
     if (*p) cudaFree(*p);
@@ -243,6 +247,7 @@ static void free_graph_arrays(Graph& g) {
     g.h_hgraph = nullptr;
     dfree(&g.degX);
     dfree(&g.lb64);
+    dfree(&g.order2);
     if (g.round_exec) cudaGraphExecDestroy(g.round_exec);
     g.round_exec = nullptr;
     if (g.ev_pool) {
@@ -611,7 +616,7 @@ int kh_hdegree_exact(kh_graph* G, int32_t* deg, uint32_t flags) {
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
-    rc = kh::launch_hdeg(g, nullptr, nullptr, g.n, g.d32, nullptr, 0, 0, s);
+    rc = kh::run_hdeg_full(g, g.d32, nullptr, 0, 0, s);
     if (rc) return rc;
     KH_CUDA_TRY(g.ctx, cudaGetLastError());
     rc = kh::copy_out(g, deg, g.d32, sizeof(int32_t) * (size_t)g.n, flags);
@@ -642,7 +647,7 @@ int kh_sampled_counts(kh_graph* G, int32_t j_lo, int32_t j_hi, int32_t* cnt, uin
     }
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
-    rc = kh::launch_hdeg(g, nullptr, nullptr, g.n, g.d32, dcnt, j_lo, nj, s);
+    rc = kh::run_hdeg_full(g, g.d32, dcnt, j_lo, nj, s);
     if (rc == KH_OK && !(flags & KH_DEVICE_PTR) && g.n > 0) {
         rc = kh::copy_out(g, cnt, dcnt, sizeof(int32_t) * (size_t)g.n * nj, 0);
     }

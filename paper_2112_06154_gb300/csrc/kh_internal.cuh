@@ -37,6 +37,9 @@ constexpr int kPhaseStride = 32;  // stamp = round * kPhaseStride + phase
 // Shared-memory visited bitmap limit per CTA (bytes); larger n uses global scratch.
 constexpr int64_t kSmemBitmapMax = 100 * 1024;
 
+// Dynamic shared memory the sliced 2-degree kernel may use per CTA (bytes).
+constexpr int64_t kSmem2Max = 220 * 1024;
+
 // Error bits written by device-side checks.
 constexpr int kErrQueue = 1;   // BFS queue overflow
 constexpr int kErrProbe = 2;   // hash probe limit reached
@@ -89,9 +92,20 @@ struct DevState {
     unsigned long long lvl_work[kMaxH + 1];
     unsigned long long lvl_changed[kMaxH + 1];
     unsigned long long stopped;
+    int tune_count;              // sample size of an autotuner measurement
 };
 
 struct Graph;
+
+// A launch layout of the whole-graph exact 2-degree pass (kh_tune.cu):
+// variant KH_VAR_CTA or KH_VAR_SLICED (KH_VAR_AUTO: not chosen yet), the
+// sliced kernel's slice count and CTA size, and the sample time it took.
+struct TuneChoice {
+    int variant;
+    int slices;
+    int threads;
+    double ms;
+};
 
 // NVTX range for profilers and tracers (a no-op unless a tool is attached).
 struct NvtxRange {
@@ -122,6 +136,23 @@ void launch_ball_hop(Graph& g, int hop, cudaStream_t s);
 // exact mode: mark the nodes of `list` (nullptr: all) stale and set their
 // lower bound max(deg_X(v), max_w deg_X(w)) <= deg_h(v; X) for h >= 2
 void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStream_t s);
+
+// ---- launchers (kh_hdeg2.cu) -------------------------------------------------
+// exact 2-degrees (and fixed-level counts when cnt != nullptr) of every node
+// with a sliced shared-memory visited set: `slices` node ranges, `threads` per
+// CTA, sources from `order` (nsrc of them).  init: deg (and cnt) are set to
+// their starting values first (every node); otherwise they must hold them.
+int launch_hdeg2_slice(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
+                       int slices, int threads, const int32_t* order, int64_t nsrc, bool init);
+// the sources of the sliced kernel, longest 2-hop work first (cached per graph)
+int ensure_order2(Graph& g, cudaStream_t s);
+size_t hdeg2_smem(int64_t width);
+// kh_tune.cu: the layout of the 2-degree pass for this graph (tuned once), and
+// the whole-graph exact h-degree / fixed-level count pass through it
+int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out);
+int run_hdeg_full(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s);
+int64_t hdeg2_width(int64_t n, int slices);
+int hdeg2_min_slices(int64_t n);
 
 // ---- launchers (kh_sampled.cu) -----------------------------------------------
 // level i of the list recursion for `count` nodes (worklist == nullptr: all);
@@ -257,6 +288,12 @@ struct Graph {
     int64_t round_exec_kernels;  // kernels in one replay of round_exec
     // kernels launched on behalf of this graph (graph replays count their nodes)
     int64_t launches;
+    // sliced 2-degree kernel: sources longest first (non-isolated nodes only)
+    int32_t *order2;
+    int64_t nsrc2;
+    // the 2-degree pass layout: forced by kh_set_variant, or chosen by the tuner
+    TuneChoice force_hdeg2;
+    TuneChoice tuned_hdeg2;
 };
 }  // namespace kh
 
@@ -271,6 +308,8 @@ int set_error(kh_ctx* ctx, int code, const char* fmt, ...);
 int ensure_work(Graph& g);
 int ensure_lists(Graph& g);
 int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps);
+// A device allocation through the context's fault-injection counter.
+int alloc_bytes(kh_ctx* ctx, void** p, size_t bytes, const char* what);
 int check_cuda(kh_ctx* ctx, cudaError_t e, const char* what);
 inline void count_launch(Graph& g, int64_t k) { g.launches += k; }
 // Profiling brackets around a launch (no-ops unless profiling is enabled).

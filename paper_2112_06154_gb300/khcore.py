@@ -29,6 +29,10 @@ KH_PROF_LEVELU = 2
 KH_PROF_FRONTIER = 3
 KH_PROF_PEEL = 4
 KH_PROF_KINDS = 5
+KH_OP_HDEG2 = 0
+KH_VAR_AUTO = 0
+KH_VAR_CTA = 1
+KH_VAR_SLICED = 2
 PROF_NAMES = ["bfs", "level1", "levelU", "frontier", "peel"]
 
 _ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",
@@ -67,6 +71,11 @@ SIGNATURES = [
     ("kh_prof_trace", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
+    ("kh_set_variant", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32]),
+    ("kh_get_variant", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]),
     ("kh_sync", ctypes.c_int, [_P]),
 ]
 
@@ -361,6 +370,21 @@ def kh_launch_count(g: Graph) -> int:
     n = ctypes.c_int64()
     _check(load().kh_launch_count(g.handle, ctypes.byref(n)), g.ctx)
     return int(n.value)
+
+
+def kh_set_variant(g: Graph, variant: int, slices: int = 0, threads: int = 0,
+                   op: int = KH_OP_HDEG2):
+    """Force the layout of the h = 2 exact-degree pass (KH_VAR_AUTO: the tuner's)."""
+    _check(load().kh_set_variant(g.handle, op, variant, slices, threads), g.ctx)
+
+
+def kh_get_variant(g: Graph, op: int = KH_OP_HDEG2):
+    """(variant, slices, threads, sample ms) of the layout in force (tunes if needed)."""
+    v, sl, th = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(load().kh_get_variant(g.handle, op, ctypes.byref(v), ctypes.byref(sl), ctypes.byref(th),
+                                 ctypes.byref(ms)), g.ctx)
+    return int(v.value), int(sl.value), int(th.value), float(ms.value)
 
 
 def kh_hdegree_exact_noalloc(rowptr, col, h: int, deg, stream=None) -> int:

@@ -1,0 +1,133 @@
+"""The two layouts of the whole-graph exact 2-degree pass and their autotuner.
+
+Every forced layout (one CTA per source; (source, slice) items with 1..64
+slices and 128..1024 threads per CTA) must give the oracle's exact 2-degrees
+(Sec. 2) and fixed-level counts element by element, on graphs with isolated
+nodes, ragged slice tails and hubs; the tuner's choice must be one of them.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_06154_gb300 import graphgen as gg
+from paper_2112_06154_gb300 import khcore as K
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    K.load(build_if_missing=True)
+    c = K.kh_ctx_create(0)
+    yield c
+    c.close()
+
+
+def _ragged():
+    # a Chung-Lu graph with isolated nodes appended (n not a multiple of 128)
+    rp, cl = gg.chung_lu(1037, 8, 2.3, 200, 55)
+    extra = 19
+    rp2 = np.concatenate([rp, np.full(extra, rp[-1], np.int64)])
+    return rp2, cl
+
+
+GRAPHS = {
+    "er": lambda: gg.erdos_renyi(2000, 8000, 1001),
+    "ragged": _ragged,
+    "cl20k": lambda: gg.chung_lu(20000, 20, 2.5, 1500, 1102),
+    "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 7),
+    "star": lambda: gg.star(300),
+    "path": lambda: gg.path(513),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_every_layout_matches_the_oracle(ctx, name):
+    rp, cl = GRAPHS[name]()
+    n = rp.size - 1
+    want = O.hdegree_exact(rp, cl, 2)
+    r = O.ranks(n, 1)
+    want_cnt = O.fixed_counts(rp, cl, r, 2, 0, 10)
+    G = K.kh_graph_load_csr(ctx, rp, cl)
+    try:
+        K.kh_set_h(G, 2)
+        layouts = [(K.KH_VAR_CTA, 0, 0)]
+        for sl in (1, 2, 3, 7, 64):
+            if sl <= n:
+                for th in (128, 256, 1024):
+                    layouts.append((K.KH_VAR_SLICED, sl, th))
+        for var, sl, th in layouts:
+            K.kh_set_variant(G, var, sl, th)
+            assert (K.kh_hdegree_exact(G) == want).all(), (var, sl, th)
+            if th in (0, 256):
+                assert (K.kh_sampled_counts(G, 0, 10) == want_cnt).all(), (var, sl, th)
+        K.kh_set_variant(G, K.KH_VAR_AUTO)
+        var, sl, th, ms = K.kh_get_variant(G)
+        assert var in (K.KH_VAR_CTA, K.KH_VAR_SLICED) and ms >= 0.0
+        assert (K.kh_hdegree_exact(G) == want).all()
+    finally:
+        G.close()
+
+
+def test_layout_arguments_are_checked(ctx):
+    rp, cl = gg.erdos_renyi(2000, 8000, 1001)
+    G = K.kh_graph_load_csr(ctx, rp, cl)
+    try:
+        for args in [(K.KH_VAR_SLICED, 0, 256), (K.KH_VAR_SLICED, 2, 100),
+                     (K.KH_VAR_SLICED, 2001, 256), (7, 1, 256)]:
+            with pytest.raises(K.KhError):
+                K.kh_set_variant(G, *args)
+        with pytest.raises(K.KhError):
+            K.kh_set_variant(G, K.KH_VAR_SLICED, 1, 256, op=5)
+    finally:
+        G.close()
+
+
+def test_large_graph_uses_slices_only(ctx):
+    # 1.2M nodes: the n-bit visited set no longer fits in shared memory
+    n = 1_200_000
+    rp0, cl0 = gg.chung_lu(40000, 12, 2.4, 2000, 31)
+    rp = np.concatenate([rp0, np.full(n - 40000, rp0[-1], np.int64)])
+    G = K.kh_graph_load_csr(ctx, rp, cl0)
+    try:
+        with pytest.raises(K.KhError):
+            K.kh_set_variant(G, K.KH_VAR_CTA)
+        var, sl, th, _ = K.kh_get_variant(G)
+        assert var == K.KH_VAR_SLICED and sl >= 1
+        deg = K.kh_hdegree_exact(G)
+        assert (deg[:40000] == O.hdegree_exact(rp0, cl0, 2)).all()
+        assert (deg[40000:] == 0).all()
+    finally:
+        G.close()
+
+
+def test_choice_table_is_written_and_reused(tmp_path):
+    table = tmp_path / "tune.txt"
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2112_06154_gb300 import graphgen as gg, khcore as K\n"
+        "K.load()\n"
+        "c = K.kh_ctx_create(0)\n"
+        "G = K.kh_graph_load_csr(c, *gg.chung_lu(20000, 20, 2.5, 1500, 1102))\n"
+        "print(*K.kh_get_variant(G))\n"
+        "G.close(); c.close()\n" % ROOT)
+    env = dict(os.environ, KH_TUNE_FILE=str(table))
+    first = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=300)
+    assert first.returncode == 0, first.stderr
+    lines = [l for l in table.read_text().splitlines() if "|" in l]
+    assert len(lines) == 1 and lines[0].startswith("hdeg2 ")
+    second = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                            text=True, timeout=300)
+    assert second.returncode == 0, second.stderr
+    # the second process reads the recorded choice (same layout and sample time)
+    assert second.stdout.split() == first.stdout.split()
+    assert len([l for l in table.read_text().splitlines() if "|" in l]) == 1
