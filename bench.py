@@ -167,6 +167,10 @@ def parse():
                    help="rmat (default) / chung_lu: headline step; rmat_ops: single operations on "
                         "R-MAT 22; batch: 4096 preferential-attachment graphs, batched vs one graph "
                         "per call; serve: a Poisson request stream through the server")
+    p.add_argument("--rmat-scale", type=int, default=22,
+                   help="--op only: R-MAT scale of the graph (a smaller case for profilers)")
+    p.add_argument("--variant", default=None,
+                   help="--op hdeg2/counts2 only: force the 2-degree layout, 'cta' or 'sliced,S,T'")
     p.add_argument("--requests", type=int, default=300)
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--pool", type=int, default=24)
@@ -475,19 +479,32 @@ def run_op(args):
     from paper_2112_06154_gb300 import khcore as K
     K.load(build_if_missing=True)
     wl = Workload(args.workload if args.workload in ("rmat", "chung_lu") else "rmat")
-    rp, cl = wl.make_graph()
+    if wl.key == "rmat" and args.rmat_scale != 22:
+        from paper_2112_06154_gb300 import graphgen as gg
+        rp, cl = gg.rmat(args.rmat_scale, 16, 0.57, 0.19, 0.19, wl.graph_seed)
+    else:
+        rp, cl = wl.make_graph()
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rp, cl)
     K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
     op, h = args.op[:-1], int(args.op[-1])
     K.kh_set_h(G, h)
+    if args.variant:
+        f = args.variant.split(",")
+        if f[0] == "cta":
+            K.kh_set_variant(G, K.KH_VAR_CTA)
+        else:
+            K.kh_set_variant(G, K.KH_VAR_SLICED, int(f[1]), int(f[2]))
     t0 = time.perf_counter()
     fn = {"hdeg": K.kh_hdegree_exact, "counts": lambda g: K.kh_sampled_counts(g, J_LO, J_HI),
           "est": K.kh_estimate, "sampled": K.kh_core_sampled, "exact": K.kh_core_exact}[op]
     fn(G)
     K.kh_sync(G)
-    print(json.dumps({"op": args.op, "seconds": time.perf_counter() - t0,
-                      "launches": K.kh_launch_count(G)}), flush=True)
+    secs = time.perf_counter() - t0
+    info = {"op": args.op, "seconds": secs, "launches": K.kh_launch_count(G), "n": int(rp.size - 1)}
+    if op in ("hdeg", "counts") and h == 2:
+        info["variant"] = K.kh_get_variant(G)
+    print(json.dumps(info), flush=True)
     G.close()
     ctx.close()
 
@@ -518,6 +535,7 @@ def run_rmat_ops(args):
         return r, time.perf_counter() - t
 
     K.kh_set_h(G, 2)
+    out["hdeg_h2_variant"] = K.kh_get_variant(G)  # tunes first
     K.kh_prof_enable(G, True)
     _, out["hdeg_h2_s"] = timed(lambda: K.kh_hdegree_exact(G))
     ms, _, b = K.kh_prof_read(G, K.KH_PROF_BFS)

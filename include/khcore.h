@@ -171,6 +171,19 @@ int kh_peel_info(kh_graph *g, int32_t *round_of, int64_t *rounds, int64_t *updat
 int kh_dense(kh_graph *g, int32_t exact, const int32_t *round_of, int32_t rounds, uint64_t *sum,
              int64_t *size, int32_t *best);
 
+/* The faster EstDense variant of Sec. 6 (after the proof of its guarantee):
+ * with k' = max_v core[v] and gamma = (1 - eps) / (1 + eps), every node with
+ * core[v] < gamma k' (compared in double precision) is removed before the
+ * replay, so the candidates are X'_q = {v kept : round_of[v] >= q}; outputs
+ * as kh_dense over those sets (size[q] = |X'_q|, a round with X'_q empty has
+ * sum 0 and is never `best`).  core: host uint64[n], the sampled core map the
+ * order came from (kh_core_sampled; an int32 exact core widened to uint64
+ * also works); kept (host uint8[n], may be NULL) receives the kept-node mask.
+ * KH_EINVAL as kh_dense, a NULL core, or eps outside (0, 1). */
+int kh_dense_pruned(kh_graph *g, int32_t exact, const int32_t *round_of, int32_t rounds,
+                    const uint64_t *core, double eps, uint64_t *sum, int64_t *size, int32_t *best,
+                    uint8_t *kept);
+
 /* Work statistics of the last kh_core_* call (no counterpart in the paper).
  * refreshed[i] / changed[i] (host int64[KH_MAX_H + 1], indexed by level i,
  * each may be NULL): level-i lists recomputed by the rounds' refresh passes

@@ -74,6 +74,9 @@ def _load():
     lib.kho_dp_level.restype = ctypes.c_int
     lib.kho_dense_curve.argtypes = [i64, P, P, P, i32, i64, i32, P, i32, P, P]
     lib.kho_dense_curve.restype = ctypes.c_int
+    lib.kho_dense_curve_pruned.argtypes = [i64, P, P, P, i32, i64, i32, P, i32, P,
+                                           ctypes.c_double, P, P, P]
+    lib.kho_dense_curve_pruned.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -235,6 +238,24 @@ def dense_curve(rowptr, col, r, h: int, M: int, exact: bool, round_of, rounds: i
     _check(_load().kho_dense_curve(n, _p(rowptr), _p(col), _p(r), h, max(M, 1), 1 if exact else 0,
                                    _p(ro), rounds, _p(total), _p(size)), "dense_curve")
     return total[:rounds], size[:rounds]
+
+
+def dense_curve_pruned(rowptr, col, r, h: int, M: int, exact: bool, round_of, rounds: int,
+                       core, eps: float):
+    """EstDense's faster variant (Sec. 6): nodes with c'(v) < gamma k' removed
+    first (gamma = (1-eps)/(1+eps), k' = max c').  Returns (sum uint64[rounds],
+    size int64[rounds], keep uint8[n]) over X'_q = {v kept : round_of[v] >= q}."""
+    rowptr, col, n = _graph(rowptr, col)
+    r = np.ascontiguousarray(r, dtype=np.uint8)
+    ro = np.ascontiguousarray(round_of, dtype=np.int32)
+    c = np.ascontiguousarray(core, dtype=np.uint64)
+    total = np.zeros(max(rounds, 1), dtype=np.uint64)
+    size = np.zeros(max(rounds, 1), dtype=np.int64)
+    keep = np.zeros(max(n, 1), dtype=np.uint8)
+    _check(_load().kho_dense_curve_pruned(n, _p(rowptr), _p(col), _p(r), h, max(M, 1),
+                                          1 if exact else 0, _p(ro), rounds, _p(c), eps,
+                                          _p(total), _p(size), _p(keep)), "dense_curve_pruned")
+    return total[:rounds], size[:rounds], keep[:n]
 
 
 def dp_level(rowptr, col, r, i: int, M: int, prev=None, v0: int = 0, v1: int = None):

@@ -26,6 +26,8 @@
  *   kho_core_sampled      Core (Alg. 4) with naive Update (Alg. 3).
  *   kho_dense_curve       EstDense (Alg. 7, Sec. 6): along a removal order, the
  *                         sum of d(v; X) over each candidate set X.
+ *   kho_dense_curve_pruned  the same after removing the nodes with
+ *                         c'(v) < gamma k' (the faster variant of Sec. 6).
  *
  * Peeling schedule.  Both peels support two schedules that must give the same
  * core map because d(v; X) never grows when X shrinks (exact: N shrinks; sampled:
@@ -946,9 +948,51 @@ int kho_estimate_def_some(int64_t n, const int64_t *rowptr, const int32_t *col,
  * (one node per round gives the paper's n candidates).  For r in [0, rounds):
  * size[r] = |X_r| and sum[r] = sum over v in X_r of d(v; X_r), where d is
  * deg_h (exact != 0) or Def. 4.1 on the rank list of N(v; h, X_r), v first. */
+static int dense_curve(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *r,
+                       int32_t h, int64_t M, int32_t exact, const int32_t *round_of,
+                       int32_t rounds, const uint8_t *keep, uint64_t *sum, int64_t *size);
+
 int kho_dense_curve(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *r,
                     int32_t h, int64_t M, int32_t exact, const int32_t *round_of, int32_t rounds,
                     uint64_t *sum, int64_t *size)
+{
+    return dense_curve(n, rowptr, col, r, h, M, exact, round_of, rounds, NULL, sum, size);
+}
+
+/* The faster variant of EstDense used in the paper's experiments (Sec. 6,
+ * after Prop. 6.2's proof): with k' = max_v c'(v) and gamma = (1 - eps) /
+ * (1 + eps), every node with c'(v) < gamma k' is removed before EstDense runs,
+ * so the candidates are X'_q = {v : c'(v) >= gamma k', round_of[v] >= q}.
+ * The comparison is made in double precision: c'(v) >= gamma * k'.
+ * keep_out (may be NULL) receives the kept-node mask. */
+int kho_dense_curve_pruned(int64_t n, const int64_t *rowptr, const int32_t *col,
+                           const uint8_t *r, int32_t h, int64_t M, int32_t exact,
+                           const int32_t *round_of, int32_t rounds, const uint64_t *core,
+                           double eps, uint64_t *sum, int64_t *size, uint8_t *keep_out)
+{
+    if (!(eps > 0.0) || !(eps < 1.0))
+        return KHO_EINVAL;
+    uint8_t *keep = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!keep)
+        return KHO_ENOMEM;
+    uint64_t kmax = 0;
+    for (int64_t v = 0; v < n; v++)
+        if (core[v] > kmax)
+            kmax = core[v];
+    double gamma = (1.0 - eps) / (1.0 + eps);
+    double thr = gamma * (double)kmax;
+    for (int64_t v = 0; v < n; v++)
+        keep[v] = (double)core[v] >= thr ? 1 : 0;
+    int rc = dense_curve(n, rowptr, col, r, h, M, exact, round_of, rounds, keep, sum, size);
+    if (keep_out)
+        memcpy(keep_out, keep, (size_t)n);
+    free(keep);
+    return rc;
+}
+
+static int dense_curve(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *r,
+                       int32_t h, int64_t M, int32_t exact, const int32_t *round_of,
+                       int32_t rounds, const uint8_t *keep, uint64_t *sum, int64_t *size)
 {
     if (rounds < 0 || (!exact && M < 1))
         return KHO_EINVAL;
@@ -972,7 +1016,7 @@ int kho_dense_curve(int64_t n, const int64_t *rowptr, const int32_t *col, const 
         int64_t cnt = 0;
         uint64_t s = 0;
         for (int64_t v = 0; v < n; v++) {
-            alive[v] = round_of[v] >= q ? 1 : 0;
+            alive[v] = (round_of[v] >= q && (!keep || keep[v])) ? 1 : 0;
             cnt += alive[v];
         }
         for (int64_t v = 0; v < n; v++) {

@@ -164,6 +164,7 @@ int ensure_lists(Graph& g) {
     if ((rc = dalloc(g.ctx, &g.lsz, (size_t)g.lvl_alloc * g.n, "list sizes"))) return rc;
     if ((rc = dalloc(g.ctx, &g.lk, (size_t)g.lvl_alloc * g.n, "list levels"))) return rc;
     if ((rc = dalloc(g.ctx, &g.rho, (size_t)g.n, "list change ranks"))) return rc;
+    if ((rc = ensure_split(g))) return rc;
     if (!g.ranks_valid) {
         launch_ranks(g, g.ctx->stream);
         g.ranks_valid = true;
@@ -230,6 +231,7 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.loss);
     dfree(&g.listL);
     dfree(&g.sched);
+    dfree(&g.keep);
     dfree(&g.dsum);
     dfree(&g.deadbm);
     dfree(&g.gid);
@@ -248,6 +250,13 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.degX);
     dfree(&g.lb64);
     dfree(&g.order2);
+    dfree(&g.part_keys);
+    dfree(&g.part_size);
+    dfree(&g.part_t);
+    dfree(&g.part_done);
+    dfree(&g.split_first);
+    dfree(&g.sub_v);
+    dfree(&g.sub_j);
     if (g.round_exec) cudaGraphExecDestroy(g.round_exec);
     g.round_exec = nullptr;
     if (g.ev_pool) {
@@ -702,32 +711,38 @@ int kh_peel_info(kh_graph* G, int32_t* round_of, int64_t* rounds, int64_t* updat
     return KH_OK;
 }
 
-int kh_dense(kh_graph* G, int32_t exact, const int32_t* round_of, int32_t rounds, uint64_t* sum,
-             int64_t* size, int32_t* best) {
-    kh::NvtxRange nvtx_range("kh_dense");
-    if (!G || !round_of) return KH_EINVAL;
-    Graph& g = G->g;
-    if (g.gid) return kh::set_error(g.ctx, KH_EINVAL, "kh_dense takes a single graph, not a batch");
+namespace kh {
+// EstDense replay of a removal order (Alg. 7); keep (host, may be nullptr):
+// nodes outside it are removed before the replay starts (the pruned variant).
+static int dense_common(Graph& g, int32_t exact, const int32_t* round_of, int32_t rounds,
+                        const uint8_t* keep, uint64_t* sum, int64_t* size, int32_t* best) {
+    if (g.gid) return set_error(g.ctx, KH_EINVAL, "kh_dense takes a single graph, not a batch");
     if (rounds < 1 || (int64_t)rounds > g.n + 1)
-        return kh::set_error(g.ctx, KH_EINVAL, "rounds must be in [1, n + 1]");
+        return set_error(g.ctx, KH_EINVAL, "rounds must be in [1, n + 1]");
     std::vector<int64_t> left((size_t)rounds + 1, 0);
     for (int64_t v = 0; v < g.n; ++v) {
         const int32_t r = round_of[v];
-        if (r < 0 || r >= rounds) return kh::set_error(g.ctx, KH_EINVAL, "round_of[%lld] = %d outside [0, rounds)", (long long)v, r);
-        left[(size_t)r] += 1;
+        if (r < 0 || r >= rounds) return set_error(g.ctx, KH_EINVAL, "round_of[%lld] = %d outside [0, rounds)", (long long)v, r);
+        if (!keep || keep[v]) left[(size_t)r] += 1;
     }
     for (int32_t q = rounds - 1; q >= 0; --q) left[(size_t)q] += left[(size_t)q + 1];  // |X_q|
     cudaSetDevice(g.ctx->device);
-    int rc = kh::ensure_work(g);
+    int rc = ensure_work(g);
     if (rc) return rc;
-    if ((rc = kh::dalloc(g.ctx, &g.sched, (size_t)g.n, "removal order"))) return rc;
-    if ((rc = kh::dalloc(g.ctx, &g.dsum, (size_t)g.n + 1, "per-round sums"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.sched, (size_t)g.n, "removal order"))) return rc;
+    if ((rc = dalloc(g.ctx, &g.dsum, (size_t)g.n + 1, "per-round sums"))) return rc;
+    if (keep && (rc = dalloc(g.ctx, &g.keep, (size_t)g.n, "kept nodes"))) return rc;
     if (g.n > 0)
         KH_CUDA_TRY(g.ctx, cudaMemcpy(g.sched, round_of, sizeof(int32_t) * (size_t)g.n, cudaMemcpyHostToDevice));
+    if (keep && g.n > 0)
+        KH_CUDA_TRY(g.ctx, cudaMemcpy(g.keep, keep, (size_t)g.n, cudaMemcpyHostToDevice));
     KH_CUDA_TRY(g.ctx, cudaMemset(g.dsum, 0, sizeof(unsigned long long) * ((size_t)g.n + 1)));
     g.dense = true;
-    rc = kh::run_core(g, exact == 0, nullptr, nullptr, false);
+    g.start_keep = keep != nullptr;
+    g.start_alive = keep ? left[0] : g.n;
+    rc = run_core(g, exact == 0, nullptr, nullptr, false);
     g.dense = false;
+    g.start_keep = false;
     if (rc) return rc;
     std::vector<unsigned long long> s((size_t)rounds);
     KH_CUDA_TRY(g.ctx, cudaMemcpy(s.data(), g.dsum, sizeof(unsigned long long) * (size_t)rounds, cudaMemcpyDeviceToHost));
@@ -743,6 +758,32 @@ int kh_dense(kh_graph* G, int32_t exact, const int32_t* round_of, int32_t rounds
     }
     if (best) *best = arg;
     return KH_OK;
+}
+}  // namespace kh
+
+int kh_dense(kh_graph* G, int32_t exact, const int32_t* round_of, int32_t rounds, uint64_t* sum,
+             int64_t* size, int32_t* best) {
+    kh::NvtxRange nvtx_range("kh_dense");
+    if (!G || !round_of) return KH_EINVAL;
+    return kh::dense_common(G->g, exact, round_of, rounds, nullptr, sum, size, best);
+}
+
+int kh_dense_pruned(kh_graph* G, int32_t exact, const int32_t* round_of, int32_t rounds,
+                    const uint64_t* core, double eps, uint64_t* sum, int64_t* size, int32_t* best,
+                    uint8_t* kept) {
+    kh::NvtxRange nvtx_range("kh_dense_pruned");
+    if (!G || !round_of || !core) return KH_EINVAL;
+    Graph& g = G->g;
+    if (!(eps > 0.0) || !(eps < 1.0)) return kh::set_error(g.ctx, KH_EINVAL, "need 0 < eps < 1");
+    // Sec. 6: drop every node with c'(v) < gamma k', gamma = (1 - eps) / (1 + eps),
+    // k' = max c' (compared in double precision)
+    uint64_t kmax = 0;
+    for (int64_t v = 0; v < g.n; ++v) kmax = core[v] > kmax ? core[v] : kmax;
+    const double thr = (1.0 - eps) / (1.0 + eps) * (double)kmax;
+    std::vector<uint8_t> keep((size_t)(g.n > 0 ? g.n : 1));
+    for (int64_t v = 0; v < g.n; ++v) keep[(size_t)v] = (double)core[v] >= thr ? 1 : 0;
+    if (kept && g.n > 0) memcpy(kept, keep.data(), (size_t)g.n);
+    return kh::dense_common(g, exact, round_of, rounds, keep.data(), sum, size, best);
 }
 
 int kh_peel_stats(kh_graph* G, int64_t* refreshed, int64_t* changed, int64_t* stopped) {

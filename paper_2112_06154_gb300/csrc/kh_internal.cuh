@@ -67,7 +67,8 @@ constexpr int kRcF = 54;           // + hop: frontier written by that hop (exact
 constexpr int kRcC = 71;           // + i: changed nodes at level i
 constexpr int kRcLossWork = 88;    // exact refresh: loss-BFS work counter
 constexpr int kRcLossCount = 89;   // exact refresh: nodes with a loss this round
-constexpr int kRcCount = 90;
+constexpr int kRcSub = 90;         // + i: split-part items of level i (0: the refine)
+constexpr int kRcCount = 107;
 
 struct DevState {
     unsigned long long c;        // current core value (max of round minima)
@@ -93,6 +94,7 @@ struct DevState {
     unsigned long long lvl_changed[kMaxH + 1];
     unsigned long long stopped;
     int tune_count;              // sample size of an autotuner measurement
+    int nSub;                    // split-part items (standalone level passes)
 };
 
 struct Graph;
@@ -272,6 +274,10 @@ struct Graph {
     bool have_rounds;
     // EstDense replay: the removal order (round per node), per-round sums of d
     bool dense;
+    // the pruned EstDense replay starts from the kept nodes only (keep[v] != 0)
+    bool start_keep;
+    int64_t start_alive;
+    uint8_t* keep;
     int32_t* sched;
     unsigned long long* dsum;
     // profiling: CUDA events around every launch of a kernel class
@@ -288,6 +294,18 @@ struct Graph {
     int64_t round_exec_kernels;  // kernels in one replay of round_exec
     // kernels launched on behalf of this graph (graph replays count their nodes)
     int64_t launches;
+    // level passes: part slots of split heavy nodes (part_cap slots of cap
+    // keys; 0 when the graph has no node above the split degree)
+    int64_t part_cap;
+    int64_t part_cap_keys;  // cap the slots were sized for
+    uint32_t *part_keys;
+    int32_t *part_size;
+    uint8_t *part_t;
+    int32_t *part_done;
+    int32_t *split_first;
+    int32_t *sub_v;
+    int32_t *sub_j;
+    bool split_planned;     // part_cap computed for this graph
     // sliced 2-degree kernel: sources longest first (non-isolated nodes only)
     int32_t *order2;
     int64_t nsrc2;
@@ -307,6 +325,8 @@ int set_error(kh_ctx* ctx, int code, const char* fmt, ...);
 // Ensure the per-graph work arrays exist (idempotent).
 int ensure_work(Graph& g);
 int ensure_lists(Graph& g);
+// part slots for the split heavy nodes of the level passes (kh_sampled.cu)
+int ensure_split(Graph& g);
 int ensure_bfs_scratch(Graph& g, int64_t ctas, bool bitmaps);
 // A device allocation through the context's fault-injection counter.
 int alloc_bytes(kh_ctx* ctx, void** p, size_t bytes, const char* what);

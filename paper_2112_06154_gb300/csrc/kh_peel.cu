@@ -183,12 +183,35 @@ __global__ void k_collect(const uint8_t* __restrict__ alive, uint8_t* __restrict
     }
 }
 
-__global__ void k_init_exact(const int64_t* __restrict__ rowptr, int64_t n, int32_t* __restrict__ degX,
-                             int32_t* __restrict__ d) {
+// Alive degrees and "no upper bound yet".  A start from a subset (alive[v]
+// from the caller) counts only alive neighbours; a start from the whole graph
+// (all alive) takes the row length.
+__global__ void k_init_exact(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const uint8_t* __restrict__ alive, int subset, int64_t n,
+                             int32_t* __restrict__ degX, int32_t* __restrict__ d) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        degX[v] = (int32_t)(rowptr[v + 1] - rowptr[v]);
+        int32_t dx = (int32_t)(rowptr[v + 1] - rowptr[v]);
+        if (subset) {
+            dx = 0;
+            for (int64_t k = rowptr[v]; k < rowptr[v + 1]; ++k) dx += alive[col[k]] == 1;
+        }
+        degX[v] = dx;
         d[v] = 0x7fffffff;  // no upper bound known yet
+    }
+}
+
+// Start from the kept nodes only: alive[v] = keep[v], removed ones in deadbm.
+// Nodes that are not kept get no removal round (-1).
+__global__ void k_init_keep(const uint8_t* __restrict__ keep, int64_t n, uint8_t* __restrict__ alive,
+                            uint32_t* __restrict__ deadbm, int32_t* __restrict__ round_of) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        alive[v] = keep[v] ? 1 : 0;
+        if (!keep[v]) {
+            atomicOr(deadbm + (v >> 5), 1u << (v & 31));
+            round_of[v] = -1;
+        }
     }
 }
 
@@ -426,7 +449,8 @@ int start_peel(Graph& g, bool sampled, cudaStream_t s) {
         KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.d64, 0xff, sizeof(unsigned long long) * (size_t)g.n, s));
         launch_stale_sampled(g, nullptr, nullptr, s);
     } else {
-        k_init_exact<<<grid, kPeelThreads, 0, s>>>(g.rowptr, g.n, g.degX, g.d32);
+        k_init_exact<<<grid, kPeelThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.start_keep ? 1 : 0,
+                                                   g.n, g.degX, g.d32);
         count_launch(g, 1);
         launch_stale_exact(g, nullptr, nullptr, s);
     }
@@ -616,6 +640,10 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.alive, 1, (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.seen, 0xff, sizeof(int32_t) * (size_t)g.n, s));
     KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.deadbm, 0, ((size_t)(g.n + 127) / 128) * 16, s));
+    if (g.start_keep && g.n > 0) {
+        k_init_keep<<<peel_grid(g), kPeelThreads, 0, s>>>(g.keep, g.n, g.alive, g.deadbm, g.round_of);
+        count_launch(g, 1);
+    }
     if (!sampled) KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.loss, 0, sizeof(int32_t) * (size_t)g.n, s));
     DevState init;
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&init, g.state, sizeof(init), cudaMemcpyDeviceToHost, s));
@@ -626,7 +654,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
     memcpy(init.bytes, keep_bytes, sizeof(keep_bytes));  // profiling counters accumulate
     init.minval = ~0ull;
     init.minU = ~0ull;
-    init.n_alive = (int)g.n;
+    init.n_alive = (int)(g.start_keep ? g.start_alive : g.n);
     KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.state, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // `init` is a host stack object
     const size_t pbytes = sizeof(unsigned long long) * (size_t)peel_graphs(g);

@@ -78,9 +78,25 @@ struct LevelArgs {
     unsigned long long* stopped;
     int8_t* rho;  // tracked passes: top rank of each changed list's changes
     unsigned long long* min_done;  // refine: per-graph minimum of the completed values
+    // split heavy nodes (k_levelU): partial sets of cap keys per part slot,
+    // their sizes and levels, parts finished per split node (at its first
+    // slot), each heavy node's first slot, the part items (part_cap 0: no split)
+    uint32_t* part_keys;
+    int32_t* part_size;
+    uint8_t* part_t;
+    int32_t* part_done;
+    int32_t* split_first;
+    int32_t* sub_v;
+    int32_t* sub_j;
+    int* n_sub;
+    int64_t part_cap;
 };
 
 constexpr int kL1Heavy = 512;
+// k_levelU splits nodes of more than kSplitDeg neighbours into parts of
+// kSplitChunk neighbours each
+constexpr int kSplitDeg = 4096;
+constexpr int kSplitChunk = 2048;
 
 // What one node computes in this launch: its level, whether that is its last
 // level h(v) (estimate) or an intermediate one (list), its M, and where its
@@ -381,6 +397,15 @@ size_t levelU_smem(int lg) {
     return hcap * 4 + (hcap >> 1) * 4 + hcap * 2;
 }
 
+// Heavy nodes (degree > kSplitDeg) are split: part j unions the lists of
+// neighbours [j kSplitChunk, (j+1) kSplitChunk) into its own trimmed partial
+// set, and the CTA that finishes a node's last part merges the partial sets.
+// The merge is exact: a part's level t_p (max of its neighbours' k[w,i-1] and
+// its own trim) is at most the node's final level kappa, because adding lists
+// only raises the counts S_j; so every member of B[v,i] (rank >= kappa) is in
+// some partial set, and for j >= t* = max_p t_p the counts S_j of the union of
+// the partial sets equal those of the full union.  The merge therefore runs the
+// same running-threshold union over the partial sets from t = t*.
 __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int hcap = 1 << lg;
@@ -390,7 +415,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     __shared__ int s_hist[32];
     __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
     __shared__ int s_vin, s_exit;                // own key in the table; early stop taken
-    __shared__ int s_rho;
+    __shared__ int s_rho, s_last;
     __shared__ unsigned long long s_T, s_part;  // early-stop threshold; partial estimate
     // flat mode (degree <= kFlatMax): per neighbour list its node, size, first
     // chunk index (exclusive prefix of 128-key chunk counts) and the first
@@ -404,7 +429,8 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kLuThreads / 32;
     const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
-    if (total == 0) return;
+    const int64_t nsub = a.n_sub ? min((int64_t)(*a.n_sub), a.part_cap) : 0;
+    if (total + nsub == 0) return;
     unsigned long long my_bytes = 0;
     // the table starts empty once per launch; every node leaves it empty again
     for (int i = tid; i < hcap; i += blockDim.x) tab[i] = kEmpty;
@@ -412,325 +438,423 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
         if (tid == 0) s_src = atomicAdd(a.work_ctr, 1);
         __syncthreads();
         const int64_t idx = s_src;
-        if (idx >= total) break;
-        const int v = a.worklist ? a.worklist[idx] : (int)idx;
-        const NodeLevel nl = node_level(a, v);
-        if (a.alive[v] != 1 || nl.skip || nl.lvl < 2) {
+        if (idx >= total + nsub) break;
+        // mode 0: a whole node; 1: one part of a split node (2: its merge)
+        int v, mode = 0, part = 0;
+        if (idx < total) {
+            v = a.worklist ? a.worklist[idx] : (int)idx;
+        } else {
+            v = a.sub_v[idx - total];
+            part = a.sub_j[idx - total];
+            mode = 1;
+        }
+        if (v < 0) {  // a part the plan could not place
             __syncthreads();
             continue;
         }
-        if (tid < 32) s_hist[tid] = 0;
-        if (tid == 0) {
-            s_t = 0;
-            s_nused = 0;
-            s_vin = 0;
-            s_exit = 0;
-            unsigned long long T = ~0ull;
-            if (a.stop_c && nl.last) {
-                const int g = a.gid ? a.gid[v] : 0;
-                T = a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g];
-            }
-            s_T = T;
-        }
-        __syncthreads();
+        const NodeLevel nl = node_level(a, v);
         const int64_t b = a.rowptr[v], e = a.rowptr[v + 1];
         const int deg = (int)(e - b);
-        const bool can_stop = s_T != ~0ull;
-        // t starts at max k[w,i-1] over alive neighbours (Prop. 3.1)
-        int myk = 0;
-        for (int64_t k = b + tid; k < e; k += blockDim.x) {
-            const int32_t w = a.col[k];
-            if (a.alive[w] == 1) myk = max(myk, (int)nl.lk_in[w]);
+        // a heavy node is done by its parts (k_split_plan gave it slots)
+        if (a.alive[v] != 1 || nl.skip || nl.lvl < 2 ||
+            (mode == 0 && a.part_cap > 0 && deg > kSplitDeg)) {
+            __syncthreads();
+            continue;
         }
-        for (int off = 16; off > 0; off >>= 1) myk = max(myk, __shfl_down_sync(kFull, myk, off));
-        if (lane == 0 && myk) atomicMax(&s_t, myk);
-        __syncthreads();
         const int rv = a.rank[v];
-        if (tid == 0 && rv >= s_t) {
-            const int slot = set_insert(tab, lg, ((uint32_t)rv << kIdBits) | (uint32_t)v, a.err);
-            if (slot >= 0) {
-                used[s_nused++] = (uint16_t)slot;
-                s_hist[rv] += 1;
-                s_vin = 1;
+        const int first = mode ? a.split_first[v] : -1;
+        const int nparts = (deg + kSplitChunk - 1) / kSplitChunk;
+        for (;;) {  // a node's last part continues as its merge (mode 2)
+            // lists: neighbours [l0, l1) (modes 0, 1) or partial sets [0, nparts) (mode 2)
+            const int l0 = mode == 1 ? part * kSplitChunk : 0;
+            const int l1 = mode == 0 ? deg : (mode == 1 ? min(deg, l0 + kSplitChunk) : nparts);
+            const int L = l1 - l0;
+            if (tid < 32) s_hist[tid] = 0;
+            if (tid == 0) {
+                s_t = 0;
+                s_nused = 0;
+                s_vin = 0;
+                s_exit = 0;
+                unsigned long long T = ~0ull;
+                if (a.stop_c && nl.last && mode == 0) {
+                    const int g = a.gid ? a.gid[v] : 0;
+                    T = a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g];
+                }
+                s_T = T;
             }
-        }
-        __syncthreads();
-        // Flat mode, degree <= kFlatMax: every (list, 128-key chunk) pair is one
-        // work item, warps take items in order, one per step, so long and short
-        // lists balance; a list is dropped once a chunk shows a key below t.
-        const bool flat = deg <= kFlatMax;
-        if (flat) {
-            int cnt = 0;
-            if (tid < deg) {
-                const int32_t w = a.col[b + tid];
-                int sz = 0;
-                if (a.alive[w] == 1) sz = min(nl.lsz_in[w], (int)a.cap);
-                s_w[tid] = w;
-                s_sz[tid] = sz;
-                s_dead[tid] = INT_MAX;
-                cnt = (sz + kChunkKeys - 1) / kChunkKeys;
-            }
-            int inc = cnt;  // block-wide exclusive scan of the chunk counts
-            for (int off = 1; off < 32; off <<= 1) {
-                const int x = __shfl_up_sync(kFull, inc, off);
-                if (lane >= off) inc += x;
-            }
-            if (lane == 31) s_wsum[warp] = inc;
             __syncthreads();
-            int before = 0;
-            for (int w2 = 0; w2 < warp; ++w2) before += s_wsum[w2];
-            if (tid < deg) s_off[tid] = before + inc - cnt;
-            if (tid == kLuThreads - 1) s_total = before + inc;
+            const bool can_stop = s_T != ~0ull;
+            // t starts at max k[w,i-1] over alive neighbours (Prop. 3.1), or at
+            // the largest level of the partial sets (merge)
+            int myk = 0;
+            for (int li = l0 + tid; li < l1; li += blockDim.x) {
+                if (mode == 2) {
+                    myk = max(myk, (int)__ldcg(a.part_t + first + li));
+                } else {
+                    const int32_t w = a.col[b + li];
+                    if (a.alive[w] == 1) myk = max(myk, (int)nl.lk_in[w]);
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) myk = max(myk, __shfl_down_sync(kFull, myk, off));
+            if (lane == 0 && myk) atomicMax(&s_t, myk);
             __syncthreads();
-        }
-        int fbase = 0;  // flat mode: first item of this step
-        // Grouped mode (high degree): G lanes share one neighbour list and read
-        // G*4 consecutive keys per step; G shrinks with degree so that many
-        // lists are open at once (hubs: one lane per list)
-        int G = 32;
-        while (G > 1 && (kLuThreads / G) < deg) G >>= 1;
-        const int ngroups = kLuThreads / G;
-        const int gid = tid / G, gl = tid % G;
-        const uint32_t gmask = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
-        const int step = kKeysPerLane * G;
-        int li = gid;  // neighbour index of this group's current list
-        int pos = 0;
-        bool any = true, stopped = false;
-        while (any) {
-            const int t = *(volatile int*)&s_t;
+            if (tid == 0 && rv >= s_t) {
+                const int slot = set_insert(tab, lg, ((uint32_t)rv << kIdBits) | (uint32_t)v, a.err);
+                if (slot >= 0) {
+                    used[s_nused++] = (uint16_t)slot;
+                    s_hist[rv] += 1;
+                    s_vin = 1;
+                }
+            }
+            __syncthreads();
+            // Flat mode, whole nodes of degree <= kFlatMax: every (list, 128-key
+            // chunk) pair is one work item, warps take items in order, one per
+            // step, so long and short lists balance; a list is dropped once a
+            // chunk shows a key below t.
+            const bool flat = mode == 0 && deg <= kFlatMax;
             if (flat) {
-                const int c = fbase + warp;
-                if (c < s_total) {
-                    int lo = 0, hi = deg - 1;  // last list whose first chunk is <= c
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_off[mid] <= c) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    // chunks after one with a key below t hold only keys below t;
-                    // warps of one step run unordered, so an earlier chunk of the
-                    // same list is still read even when a later one was seen first
-                    if (c <= __shfl_sync(kFull, s_dead[lo], 0)) {
-                        const int sz = s_sz[lo];
-                        const int p = (c - s_off[lo]) * kChunkKeys + lane * kKeysPerLane;
-                        bool below = false;
-                        if (p < sz) {
-                            const uint4 k4 = *reinterpret_cast<const uint4*>(
-                                nl.keys_in + (size_t)s_w[lo] * (size_t)a.cap + p);
-                            const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+                int cnt = 0;
+                if (tid < deg) {
+                    const int32_t w = a.col[b + tid];
+                    int sz = 0;
+                    if (a.alive[w] == 1) sz = min(nl.lsz_in[w], (int)a.cap);
+                    s_w[tid] = w;
+                    s_sz[tid] = sz;
+                    s_dead[tid] = INT_MAX;
+                    cnt = (sz + kChunkKeys - 1) / kChunkKeys;
+                }
+                int inc = cnt;  // block-wide exclusive scan of the chunk counts
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int x = __shfl_up_sync(kFull, inc, off);
+                    if (lane >= off) inc += x;
+                }
+                if (lane == 31) s_wsum[warp] = inc;
+                __syncthreads();
+                int before = 0;
+                for (int w2 = 0; w2 < warp; ++w2) before += s_wsum[w2];
+                if (tid < deg) s_off[tid] = before + inc - cnt;
+                if (tid == kLuThreads - 1) s_total = before + inc;
+                __syncthreads();
+            }
+            int fbase = 0;  // flat mode: first item of this step
+            // Grouped mode: G lanes share one list and read G*4 consecutive keys
+            // per step; G shrinks as the number of lists grows, so that many
+            // lists are open at once (hubs: one lane per list)
+            int G = 32;
+            while (G > 1 && (kLuThreads / G) < L) G >>= 1;
+            const int ngroups = kLuThreads / G;
+            const int gid = tid / G, gl = tid % G;
+            const uint32_t gmask = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+            const int step = kKeysPerLane * G;
+            int li = l0 + gid;  // list index of this group's current list
+            int pos = 0;
+            bool any = true, stopped = false;
+            while (any) {
+                const int t = *(volatile int*)&s_t;
+                if (flat) {
+                    const int c = fbase + warp;
+                    if (c < s_total) {
+                        int lo = 0, hi = deg - 1;  // last list whose first chunk is <= c
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_off[mid] <= c) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        // chunks after one with a key below t hold only keys below t;
+                        // warps of one step run unordered, so an earlier chunk of the
+                        // same list is still read even when a later one was seen first
+                        if (c <= __shfl_sync(kFull, s_dead[lo], 0)) {
+                            const int sz = s_sz[lo];
+                            const int p = (c - s_off[lo]) * kChunkKeys + lane * kKeysPerLane;
+                            bool below = false;
+                            if (p < sz) {
+                                const uint4 k4 = *reinterpret_cast<const uint4*>(
+                                    nl.keys_in + (size_t)s_w[lo] * (size_t)a.cap + p);
+                                const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
-                            for (int q = 0; q < kKeysPerLane; ++q) {
-                                if (p + q < sz) {
-                                    const uint32_t key = kk[q];
-                                    const int r = (int)(key >> kIdBits);
-                                    my_bytes += 4;
-                                    if (r >= t) {
-                                        const int slot = set_insert(tab, lg, key, a.err);
-                                        if (slot >= 0) {
-                                            const int u = atomicAdd(&s_nused, 1);
-                                            if (u < hcap) used[u] = (uint16_t)slot;
-                                            else atomicOr(a.err, kErrProbe);
-                                            atomicAdd(&s_hist[r], 1);
+                                for (int q = 0; q < kKeysPerLane; ++q) {
+                                    if (p + q < sz) {
+                                        const uint32_t key = kk[q];
+                                        const int r = (int)(key >> kIdBits);
+                                        my_bytes += 4;
+                                        if (r >= t) {
+                                            const int slot = set_insert(tab, lg, key, a.err);
+                                            if (slot >= 0) {
+                                                const int u = atomicAdd(&s_nused, 1);
+                                                if (u < hcap) used[u] = (uint16_t)slot;
+                                                else atomicOr(a.err, kErrProbe);
+                                                atomicAdd(&s_hist[r], 1);
+                                            }
+                                        } else {
+                                            below = true;
                                         }
-                                    } else {
-                                        below = true;
                                     }
                                 }
                             }
+                            // ranks only fall along a list: the rest of it is below t
+                            if (__any_sync(kFull, below) && lane == 0) atomicMin(&s_dead[lo], c);
                         }
-                        // ranks only fall along a list: the rest of it is below t
-                        if (__any_sync(kFull, below) && lane == 0) atomicMin(&s_dead[lo], c);
                     }
+                    fbase += nwarps;
                 }
-                fbase += nwarps;
-            }
-            // advance to an alive neighbour with a non-empty list (group-uniform)
-            int32_t w = -1;
-            int sz = 0;
-            while (!flat && li < deg) {
-                w = a.col[b + li];
-                if (a.alive[w] == 1) {
-                    sz = min(nl.lsz_in[w], (int)a.cap);
-                    if (sz > pos) break;
+                // advance to a list with keys left (group-uniform)
+                const uint32_t* lp = nullptr;
+                int sz = 0;
+                while (!flat && li < l1) {
+                    if (mode == 2) {
+                        sz = __ldcg(a.part_size + first + li);
+                        lp = a.part_keys + (size_t)(first + li) * (size_t)a.cap;
+                        if (sz > pos) break;
+                    } else {
+                        const int32_t w = a.col[b + li];
+                        if (a.alive[w] == 1) {
+                            sz = min(nl.lsz_in[w], (int)a.cap);
+                            lp = nl.keys_in + (size_t)w * (size_t)a.cap;
+                            if (sz > pos) break;
+                        }
+                    }
+                    li += ngroups;
+                    pos = 0;
                 }
-                li += ngroups;
-                pos = 0;
-            }
-            bool below = false;
-            if (!flat && li < deg) {
-                const int p = pos + gl * kKeysPerLane;
-                if (p < sz) {
-                    const uint4 k4 =
-                        *reinterpret_cast<const uint4*>(nl.keys_in + (size_t)w * (size_t)a.cap + p);
-                    const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+                bool below = false;
+                if (!flat && li < l1) {
+                    const int p = pos + gl * kKeysPerLane;
+                    if (p < sz) {
+                        const uint4 k4 = mode == 2 ? __ldcg(reinterpret_cast<const uint4*>(lp + p))
+                                                   : *reinterpret_cast<const uint4*>(lp + p);
+                        const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
-                    for (int q = 0; q < kKeysPerLane; ++q) {
-                        if (p + q < sz) {
-                            const uint32_t key = kk[q];
-                            const int r = (int)(key >> kIdBits);
-                            my_bytes += 4;
-                            if (r >= t) {
-                                const int slot = set_insert(tab, lg, key, a.err);
-                                if (slot >= 0) {
-                                    const int u = atomicAdd(&s_nused, 1);
-                                    if (u < hcap) used[u] = (uint16_t)slot;
-                                    else atomicOr(a.err, kErrProbe);
-                                    atomicAdd(&s_hist[r], 1);
+                        for (int q = 0; q < kKeysPerLane; ++q) {
+                            if (p + q < sz) {
+                                const uint32_t key = kk[q];
+                                const int r = (int)(key >> kIdBits);
+                                if (mode != 2) my_bytes += 4;
+                                if (r >= t) {
+                                    const int slot = set_insert(tab, lg, key, a.err);
+                                    if (slot >= 0) {
+                                        const int u = atomicAdd(&s_nused, 1);
+                                        if (u < hcap) used[u] = (uint16_t)slot;
+                                        else atomicOr(a.err, kErrProbe);
+                                        atomicAdd(&s_hist[r], 1);
+                                    }
+                                } else {
+                                    below = true;
                                 }
-                            } else {
-                                below = true;
                             }
                         }
                     }
                 }
-            }
-            const uint32_t bal = __ballot_sync(kFull, below);
-            if (!flat && li < deg) {
-                if ((bal & gmask) || pos + step >= sz) {
-                    li += ngroups;
-                    pos = 0;
-                } else {
-                    pos += step;
-                }
-            }
-            any = __syncthreads_or(flat ? fbase < s_total : li < deg);
-            if (warp == 0) {
-                // smallest level >= t with at most M distinct members (Alg. 5's
-                // trim): lane j holds S_j = #{distinct keys with rank >= j}
-                int S = s_hist[lane];
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int x = __shfl_down_sync(kFull, S, off);
-                    if (lane + off < 32) S += x;
-                }
-                const uint32_t over = __ballot_sync(kFull, S > nl.M);
-                const int pmax = over ? 31 - __clz(over) : -1;
-                if (can_stop) {
-                    // Def. 4.1 on the keys inserted so far plus v itself: a subset
-                    // of N(v;h) led by v, so by Prop. 4.2 at most the final estimate
-                    const int Sp = S + ((!s_vin && rv >= lane) ? 1 : 0);
-                    const uint32_t fits = __ballot_sync(kFull, Sp <= nl.M);
-                    const int k = fits ? __ffs(fits) - 1 : 32;
-                    const int Sk = __shfl_sync(kFull, Sp, k & 31);
-                    const unsigned long long part = estimate_of(k < 32 ? Sk : 0, k, rv, nl.M);
-                    if (lane == 0 && part > s_T) {
-                        s_exit = 1;
-                        s_part = part;
+                const uint32_t bal = __ballot_sync(kFull, below);
+                if (!flat && li < l1) {
+                    if ((bal & gmask) || pos + step >= sz) {
+                        li += ngroups;
+                        pos = 0;
+                    } else {
+                        pos += step;
                     }
                 }
-                if (lane == 0) {
-                    const int told = s_t;
-                    s_t = max(told, pmax + 1);
-                    s_compact = s_nused > (hcap >> 1);
-                    s_nstage = 0;
+                any = __syncthreads_or(flat ? fbase < s_total : li < l1);
+                if (warp == 0) {
+                    // smallest level >= t with at most M distinct members (Alg. 5's
+                    // trim): lane j holds S_j = #{distinct keys with rank >= j}
+                    int S = s_hist[lane];
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const int x = __shfl_down_sync(kFull, S, off);
+                        if (lane + off < 32) S += x;
+                    }
+                    const uint32_t over = __ballot_sync(kFull, S > nl.M);
+                    const int pmax = over ? 31 - __clz(over) : -1;
+                    if (can_stop) {
+                        // Def. 4.1 on the keys inserted so far plus v itself: a subset
+                        // of N(v;h) led by v, so by Prop. 4.2 at most the final estimate
+                        const int Sp = S + ((!s_vin && rv >= lane) ? 1 : 0);
+                        const uint32_t fits = __ballot_sync(kFull, Sp <= nl.M);
+                        const int k = fits ? __ffs(fits) - 1 : 32;
+                        const int Sk = __shfl_sync(kFull, Sp, k & 31);
+                        const unsigned long long pe = estimate_of(k < 32 ? Sk : 0, k, rv, nl.M);
+                        if (lane == 0 && pe > s_T) {
+                            s_exit = 1;
+                            s_part = pe;
+                        }
+                    }
+                    if (lane == 0) {
+                        const int told = s_t;
+                        s_t = max(told, pmax + 1);
+                        s_compact = s_nused > (hcap >> 1);
+                        s_nstage = 0;
+                    }
+                }
+                __syncthreads();
+                if (s_exit && any) {  // (with every list read, finish: the exact value is kept)
+                    stopped = true;
+                    break;
+                }
+                if (s_compact) {
+                    // drop keys below t: empty their slots, re-insert the rest
+                    const int tc = s_t, nu = min(s_nused, hcap);
+                    for (int i = tid; i < nu; i += blockDim.x) {
+                        const int slot = used[i];
+                        const uint32_t key = tab[slot];
+                        tab[slot] = kEmpty;
+                        if ((int)(key >> kIdBits) >= tc) {
+                            const int p = atomicAdd(&s_nstage, 1);
+                            if (p < (hcap >> 1)) stage[p] = key;
+                            else atomicOr(a.err, kErrProbe);
+                        }
+                    }
+                    __syncthreads();
+                    if (tid == 0) s_nused = 0;
+                    __syncthreads();
+                    const int ns = min(s_nstage, hcap >> 1);
+                    for (int i = tid; i < ns; i += blockDim.x) {
+                        const int slot = set_insert(tab, lg, stage[i], a.err);
+                        if (slot >= 0) used[atomicAdd(&s_nused, 1)] = (uint16_t)slot;
+                    }
+                    __syncthreads();
                 }
             }
-            __syncthreads();
-            if (s_exit && any) {  // (with every list read, finish: the exact value is kept)
-                stopped = true;
+            if (stopped) {
+                // d(v) > T: v stays stale, its lower bound raised to the partial estimate
+                const int nu = min(s_nused, hcap);
+                for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
+                if (tid == 0) {
+                    a.lb[v] = s_part;
+                    a.fresh[v] = 0;
+                    atomicAdd(a.stopped, 1ull);  // a lower bound only: not an update
+                    my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
+                }
                 break;
             }
-            if (s_compact) {
-                // drop keys below t: empty their slots, re-insert the rest
-                const int tc = s_t, nu = min(s_nused, hcap);
+            const int kappa = s_t;
+            const int nu = min(s_nused, hcap);
+            int S = 0;
+            for (int j = kappa; j < 32; ++j) S += s_hist[j];
+            __syncthreads();
+            if (mode == 1) {
+                // this part's trimmed set, grouped by rank (highest first), and its level
+                if (tid < 32) {
+                    int above = 0;
+                    for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
+                    s_hist[tid] = above;
+                }
+                __syncthreads();
+                uint32_t* out = a.part_keys + (size_t)(first + part) * (size_t)a.cap;
                 for (int i = tid; i < nu; i += blockDim.x) {
                     const int slot = used[i];
                     const uint32_t key = tab[slot];
                     tab[slot] = kEmpty;
-                    if ((int)(key >> kIdBits) >= tc) {
-                        const int p = atomicAdd(&s_nstage, 1);
-                        if (p < (hcap >> 1)) stage[p] = key;
-                        else atomicOr(a.err, kErrProbe);
+                    const int r = (int)(key >> kIdBits);
+                    if (r >= kappa) {
+                        const int p = atomicAdd(&s_hist[r], 1);
+                        if (p < a.cap) out[p] = key;
+                        else atomicOr(a.err, kErrList);
                     }
                 }
-                __syncthreads();
-                if (tid == 0) s_nused = 0;
-                __syncthreads();
-                const int ns = min(s_nstage, hcap >> 1);
-                for (int i = tid; i < ns; i += blockDim.x) {
-                    const int slot = set_insert(tab, lg, stage[i], a.err);
-                    if (slot >= 0) used[atomicAdd(&s_nused, 1)] = (uint16_t)slot;
+                if (tid == 0) {
+                    a.part_size[first + part] = S;
+                    a.part_t[first + part] = (uint8_t)kappa;
+                    my_bytes += 10ull * (unsigned long long)L;
                 }
+                __threadfence();
                 __syncthreads();
+                if (tid == 0) s_last = atomicAdd(a.part_done + first, 1) == nparts - 1;
+                __syncthreads();
+                if (!s_last) break;
+                __threadfence();  // the other parts' sets are visible from here on
+                mode = 2;
+                continue;
             }
-        }
-        if (stopped) {
-            // d(v) > T: v stays stale, its lower bound raised to the partial estimate
-            const int nu = min(s_nused, hcap);
-            for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
-            if (tid == 0) {
-                a.lb[v] = s_part;
-                a.fresh[v] = 0;
-                atomicAdd(a.stopped, 1ull);  // a lower bound only: not an update
-                my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
-            }
-            __syncthreads();
-            continue;
-        }
-        const int kappa = s_t;
-        const int nu = min(s_nused, hcap);
-        int S = 0;
-        for (int j = kappa; j < 32; ++j) S += s_hist[j];
-        __syncthreads();
-        if (tid == 0) my_bytes += 8ull + 10ull * (unsigned long long)deg + 5ull;
-        if (nl.last) {
-            if (tid == 0) {
-                const unsigned long long e = estimate_of(S, kappa, rv, nl.M);
-                a.est[v] = e;
-                if (a.min_done) atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), e);
-                record_change(a, nl, v, S, kappa);
-                atomicAdd(a.updates, 1ull);
-                my_bytes += 8;
-            }
-            for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
-        } else {
-            if (a.track) {
-                // rho (see level1_rho_warp): an old member left iff its key is
-                // not in the new union, where every key of rank >= kappa is kept
-                const int old_s = nl.lsz_out[v], old_k = nl.lk_out[v];
-                if (old_s != S || old_k != kappa) {
-                    if (tid == 0) s_rho = kappa != old_k ? old_k - 1 : -1;
-                    __syncthreads();
-                    const uint32_t* old = nl.keys_out + (size_t)v * (size_t)a.cap;
-                    const int m = min(old_s, (int)a.cap);
-                    int r = -1;
-                    for (int p = tid; p < m; p += blockDim.x) {
-                        const uint32_t key = old[p];
-                        if (!set_contains(tab, lg, key)) r = max(r, (int)(key >> kIdBits));
+            if (tid == 0) my_bytes += 8ull + 5ull + (mode == 0 ? 10ull * (unsigned long long)deg : 0ull);
+            if (nl.last) {
+                if (tid == 0) {
+                    const unsigned long long est = estimate_of(S, kappa, rv, nl.M);
+                    a.est[v] = est;
+                    if (a.min_done) atomicMin(a.min_done + (a.gid ? a.gid[v] : 0), est);
+                    record_change(a, nl, v, S, kappa);
+                    atomicAdd(a.updates, 1ull);
+                    my_bytes += 8;
+                }
+                for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
+            } else {
+                if (a.track) {
+                    // rho (see level1_rho_warp): an old member left iff its key is
+                    // not in the new union, where every key of rank >= kappa is kept
+                    const int old_s = nl.lsz_out[v], old_k = nl.lk_out[v];
+                    if (old_s != S || old_k != kappa) {
+                        if (tid == 0) s_rho = kappa != old_k ? old_k - 1 : -1;
+                        __syncthreads();
+                        const uint32_t* old = nl.keys_out + (size_t)v * (size_t)a.cap;
+                        const int m = min(old_s, (int)a.cap);
+                        int r = -1;
+                        for (int p = tid; p < m; p += blockDim.x) {
+                            const uint32_t key = old[p];
+                            if (!set_contains(tab, lg, key)) r = max(r, (int)(key >> kIdBits));
+                        }
+                        for (int off = 16; off > 0; off >>= 1) r = max(r, __shfl_xor_sync(kFull, r, off));
+                        if (lane == 0 && r >= 0) atomicMax(&s_rho, r);
+                        __syncthreads();  // the old list is read before it is overwritten
+                        if (tid == 0) a.rho[v] = (int8_t)s_rho;
                     }
-                    for (int off = 16; off > 0; off >>= 1) r = max(r, __shfl_xor_sync(kFull, r, off));
-                    if (lane == 0 && r >= 0) atomicMax(&s_rho, r);
-                    __syncthreads();  // the old list is read before it is overwritten
-                    if (tid == 0) a.rho[v] = (int8_t)s_rho;
+                }
+                // write members grouped by rank, highest first, emptying the table
+                if (tid < 32) {
+                    int above = 0;
+                    for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
+                    s_hist[tid] = above;  // start offset of rank tid
+                }
+                __syncthreads();
+                uint32_t* out = nl.keys_out + (size_t)v * (size_t)a.cap;
+                for (int i = tid; i < nu; i += blockDim.x) {
+                    const int slot = used[i];
+                    const uint32_t key = tab[slot];
+                    tab[slot] = kEmpty;
+                    const int r = (int)(key >> kIdBits);
+                    if (r >= kappa) {
+                        const int p = atomicAdd(&s_hist[r], 1);
+                        if (p < a.cap) out[p] = key;
+                        else atomicOr(a.err, kErrList);
+                    }
+                }
+                if (tid == 0) {
+                    record_change(a, nl, v, S, kappa);
+                    my_bytes += 4ull * (unsigned long long)S;
                 }
             }
-            // write members grouped by rank, highest first, emptying the table
-            if (tid < 32) {
-                int above = 0;
-                for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
-                s_hist[tid] = above;  // start offset of rank tid
-            }
-            __syncthreads();
-            uint32_t* out = nl.keys_out + (size_t)v * (size_t)a.cap;
-            for (int i = tid; i < nu; i += blockDim.x) {
-                const int slot = used[i];
-                const uint32_t key = tab[slot];
-                tab[slot] = kEmpty;
-                const int r = (int)(key >> kIdBits);
-                if (r >= kappa) {
-                    const int p = atomicAdd(&s_hist[r], 1);
-                    if (p < a.cap) out[p] = key;
-                    else atomicOr(a.err, kErrList);
-                }
-            }
-            if (tid == 0) {
-                record_change(a, nl, v, S, kappa);
-                my_bytes += 4ull * (unsigned long long)S;
-            }
+            if (mode == 2 && tid == 0) a.part_done[first] = 0;  // ready for the next launch
+            break;
         }
         __syncthreads();
     }
     for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
+}
+
+// Plan the split of the heavy nodes of a level pass: every listed node that
+// computes a level >= 2 and has more than kSplitDeg neighbours gets
+// ceil(deg / kSplitChunk) consecutive part slots and part items.
+__global__ void k_split_plan(LevelArgs a) {
+    const int64_t total = a.worklist ? (int64_t)(*a.d_count) : a.count_static;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const int v = a.worklist ? a.worklist[idx] : (int)idx;
+        const int64_t deg = a.rowptr[v + 1] - a.rowptr[v];
+        if (deg <= kSplitDeg || a.alive[v] != 1) continue;
+        const NodeLevel nl = node_level(a, v);
+        if (nl.skip || nl.lvl < 2) continue;
+        const int P = (int)((deg + kSplitChunk - 1) / kSplitChunk);
+        const int base = atomicAdd(a.n_sub, P);
+        if ((int64_t)base + P <= a.part_cap) {
+            for (int j = 0; j < P; ++j) {
+                a.sub_v[base + j] = v;
+                a.sub_j[base + j] = j;
+            }
+            a.split_first[v] = base;
+        } else {
+            // cannot happen: part_cap covers every heavy node of the graph at once
+            for (int64_t j = base; j < a.part_cap && j < (int64_t)base + P; ++j) a.sub_v[j] = -1;
+            atomicOr(a.err, kErrList);
+        }
+    }
 }
 
 // Rank filter for the neighbours of changed lists.  Level i of u is the
@@ -872,6 +996,72 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
 
 }  // namespace
 
+namespace {
+// Part slots a whole-graph level pass needs: ceil(deg / kSplitChunk) per node
+// of degree above kSplitDeg.
+__global__ void k_count_parts(const int64_t* __restrict__ rowptr, int64_t n,
+                              unsigned long long* out) {
+    unsigned long long c = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t deg = rowptr[v + 1] - rowptr[v];
+        if (deg > kSplitDeg) c += (unsigned long long)((deg + kSplitChunk - 1) / kSplitChunk);
+    }
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(kFull, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+}  // namespace
+
+int ensure_split(Graph& g) {
+    cudaStream_t s = g.ctx->stream;
+    if (!g.split_planned) {
+        unsigned long long* d = nullptr;
+        unsigned long long parts = 0;
+        KH_CUDA_TRY(g.ctx, cudaMallocAsync((void**)&d, sizeof(unsigned long long), s));
+        cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess && g.n > 0) {
+            k_count_parts<<<g.ctx->sm_count * 4, 256, 0, s>>>(g.rowptr, g.n, d);
+            count_launch(g, 1);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&parts, d, sizeof(parts), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(d, s);
+        if (e != cudaSuccess) return check_cuda(g.ctx, e, "count split parts");
+        g.part_cap = (int64_t)parts;
+        g.split_planned = true;
+    }
+    if (g.part_cap == 0) return KH_OK;
+    if (g.part_keys && g.part_cap_keys < g.cap) {
+        KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
+        cudaFree(g.part_keys);
+        g.part_keys = nullptr;
+    }
+    int rc;
+    if (!g.part_keys) {
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.part_keys,
+                              sizeof(uint32_t) * (size_t)g.part_cap * (size_t)g.cap, "split part keys")))
+            return rc;
+        g.part_cap_keys = g.cap;
+    }
+    const size_t pc = (size_t)g.part_cap;
+    if (!g.part_done) {
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.part_done, sizeof(int32_t) * pc, "split part counters")))
+            return rc;
+        KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.part_done, 0, sizeof(int32_t) * pc, s));
+    }
+    if (!g.part_size && (rc = alloc_bytes(g.ctx, (void**)&g.part_size, sizeof(int32_t) * pc, "split part sizes")))
+        return rc;
+    if (!g.part_t && (rc = alloc_bytes(g.ctx, (void**)&g.part_t, pc, "split part levels"))) return rc;
+    if (!g.sub_v && (rc = alloc_bytes(g.ctx, (void**)&g.sub_v, sizeof(int32_t) * pc, "split part nodes")))
+        return rc;
+    if (!g.sub_j && (rc = alloc_bytes(g.ctx, (void**)&g.sub_j, sizeof(int32_t) * pc, "split part indices")))
+        return rc;
+    if (!g.split_first &&
+        (rc = alloc_bytes(g.ctx, (void**)&g.split_first, sizeof(int32_t) * (size_t)g.n, "split first slots")))
+        return rc;
+    return KH_OK;
+}
+
 int table_lg(int64_t M) {
     // capacity >= 2 (M + keys inserted per step) rounded up to a power of two
     int lg = 10;
@@ -924,15 +1114,26 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
         a.n_changed = rc + kRcC + level;
         a.n_heavy = rc + kRcLevelHeavy + level;
         a.work_ctr = rc + kRcLevelWork + level;
+        a.n_sub = rc + kRcSub + level;
     } else if (round_mode == 2) {
         a.n_changed = rc + kRcC + 0;  // unused: the refine does not track changes
         a.n_heavy = rc + kRcRefineHeavy;
         a.work_ctr = rc + kRcRefineWork;
+        a.n_sub = rc + kRcSub + 0;
     } else {
         a.n_changed = &g.state->nC[level & 1];
         a.n_heavy = &g.state->nH;
         a.work_ctr = &g.state->work_ctr[1];
+        a.n_sub = &g.state->nSub;
     }
+    a.part_cap = g.part_cap;
+    a.part_keys = g.part_keys;
+    a.part_size = g.part_size;
+    a.part_t = g.part_t;
+    a.part_done = g.part_done;
+    a.split_first = g.split_first;
+    a.sub_v = g.sub_v;
+    a.sub_j = g.sub_j;
     cudaError_t e;
     if (track && round_mode == 0) {
         e = cudaMemsetAsync(a.n_changed, 0, sizeof(int), s);
@@ -974,8 +1175,21 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     if (round_mode == 0) {
         e = cudaMemsetAsync(a.work_ctr, 0, sizeof(int), s);
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset work_ctr");
+        if (g.part_cap > 0) {
+            e = cudaMemsetAsync(a.n_sub, 0, sizeof(int), s);
+            if (e != cudaSuccess) return check_cuda(g.ctx, e, "memset n_sub");
+        }
     }
     prof_begin(g, kProfLevelU, s);
+    if (g.part_cap > 0) {
+        k_split_plan<<<g.ctx->sm_count * 2, 256, 0, s>>>(a);
+        count_launch(g, 1);
+        // parts need CTAs of their own beyond the node count
+        const int64_t cap = (int64_t)g.ctx->sm_count * per_sm;
+        grid = cap;
+    } else {
+        a.n_sub = nullptr;
+    }
     k_levelU<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
     count_launch(g, 1);
     prof_end(g, kProfLevelU, s);

@@ -18,6 +18,8 @@ available offline):
   deduplicated, self-loops dropped, vertex ids permuted by a seeded permutation.
 * ``barabasi_albert(n, m)``: preferential attachment (copy model), deduplicated.
 * ``grid(a, b, shortcut_frac)``: a x b lattice plus random shortcut edges.
+* ``with_hubs(n, hub_degrees)``: a Chung-Lu graph plus a few nodes of given
+  (large) degree.
 * closed-form graphs: complete, path, cycle, star, grid.
 """
 from __future__ import annotations
@@ -27,7 +29,7 @@ import numpy as np
 __all__ = [
     "csr_from_edges", "erdos_renyi", "chung_lu", "rmat", "barabasi_albert",
     "grid", "complete", "path", "cycle", "star", "random_small",
-    "pack_batch", "graph_stats", "barabasi_albert_batch", "ba_batch_workload",
+    "pack_batch", "graph_stats", "barabasi_albert_batch", "ba_batch_workload", "with_hubs",
 ]
 
 
@@ -158,6 +160,21 @@ def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int):
         v[s:e] = vv
     perm = rng.permutation(n).astype(np.int64)
     return csr_from_edges(n, perm[u], perm[v])
+
+
+def with_hubs(n: int, hub_degrees, seed: int, avg_deg: float = 6, gamma: float = 2.3,
+              max_deg: int = 300):
+    """A Chung-Lu graph (as in chung_lu) plus hub nodes: node ``10 * i + 5`` gets
+    ``hub_degrees[i]`` extra neighbours drawn uniformly without replacement
+    (duplicates with existing edges collapse)."""
+    rp, cl = chung_lu(n, avg_deg, gamma, max_deg, seed)
+    rng = np.random.default_rng(seed + 1)
+    us = [np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))]
+    vs = [cl.astype(np.int64)]
+    for i, k in enumerate(hub_degrees):
+        us.append(np.full(int(k), 10 * i + 5, dtype=np.int64))
+        vs.append(rng.choice(n, size=int(k), replace=False).astype(np.int64))
+    return csr_from_edges(n, np.concatenate(us), np.concatenate(vs))
 
 
 def barabasi_albert(n: int, m: int, seed: int):

@@ -68,6 +68,8 @@ SIGNATURES = [
     ("kh_peel_stats", ctypes.c_int, [_P, _P, _P, _I64P]),
     ("kh_dense", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
                                 ctypes.POINTER(ctypes.c_int32)]),
+    ("kh_dense_pruned", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_double,
+                                       _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
     ("kh_prof_trace", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
@@ -322,6 +324,23 @@ def kh_dense(g: Graph, exact: bool, round_of, rounds: int):
     _check(load().kh_dense(g.handle, 1 if exact else 0, ro.ctypes.data, rounds, total.ctypes.data,
                            size.ctypes.data, ctypes.byref(best)), g.ctx)
     return total[:rounds], size[:rounds], int(best.value)
+
+
+def kh_dense_pruned(g: Graph, exact: bool, round_of, rounds: int, core, eps: float):
+    """EstDense after dropping nodes with core < gamma max(core) (Sec. 6):
+    (sum uint64[rounds], size int64[rounds], best, kept uint8[n])."""
+    ro = np.ascontiguousarray(round_of, dtype=np.int32)
+    c = np.ascontiguousarray(core, dtype=np.uint64)
+    if ro.size != g.n or c.size != g.n:
+        raise KhError(KH_EINVAL, f"round_of and core need {g.n} entries")
+    total = np.zeros(max(rounds, 1), np.uint64)
+    size = np.zeros(max(rounds, 1), np.int64)
+    kept = np.zeros(max(g.n, 1), np.uint8)
+    best = ctypes.c_int32(-1)
+    _check(load().kh_dense_pruned(g.handle, 1 if exact else 0, ro.ctypes.data, rounds,
+                                  c.ctypes.data, eps, total.ctypes.data, size.ctypes.data,
+                                  ctypes.byref(best), kept.ctypes.data), g.ctx)
+    return total[:rounds], size[:rounds], int(best.value), kept[:g.n]
 
 
 def kh_peel_stats(g: Graph):

@@ -8,8 +8,10 @@ with rank seed 1 and M from Eq. (buffer) at eps = 0.5, delta = 0.05, and
 records, per output vector, the SHA-256 of its raw little-endian bytes in
 ``fullsize_sha256.txt`` (next to this script).  The GPU tests hash the
 library's output the same way, so an equal digest means an equal vector,
-element by element.  The vectors themselves go to ``_cache/`` (not committed)
-for a per-element comparison when a digest differs.
+element by element.  The vectors themselves go to a cache folder (``--cache``,
+default ``_cache/`` next to this script, not committed; also read from the
+environment variable KH_ORACLE_CACHE) for a per-element comparison when a
+digest differs; it holds the intermediate level lists too (several GB for C3).
 
 Each oracle routine stays single-threaded; independent ranges of nodes run in
 separate processes (``--jobs``):
@@ -19,7 +21,7 @@ separate processes (``--jobs``):
   est    the level recursion (Prop. 3.1, Alg. 2) level by level with
          oracle.dp_level over node ranges, then Alg. 1: est, k[v,h], |B[v,h]|.
 
-Usage: python tests/golden/make_fullsize.py [--jobs 8] [case ...]
+Usage: python tests/golden/make_fullsize.py [--jobs 8] [--cache DIR] [case ...]
 """
 from __future__ import annotations
 
@@ -34,7 +36,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
-CACHE = os.path.join(HERE, "_cache")
+CACHE = os.environ.get("KH_ORACLE_CACHE") or os.path.join(HERE, "_cache")
 DIGESTS = os.path.join(HERE, "fullsize_sha256.txt")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -186,8 +188,13 @@ def read_digests():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=os.cpu_count() or 4)
+    ap.add_argument("--cache", default=None)
     ap.add_argument("cases", nargs="*")
     args = ap.parse_args()
+    global CACHE
+    if args.cache:
+        CACHE = os.path.abspath(args.cache)
+        os.environ["KH_ORACLE_CACHE"] = CACHE  # the spawned workers read it too
     os.makedirs(CACHE, exist_ok=True)
     todo = args.cases or list(CASES)
     rows = read_digests()

@@ -107,3 +107,31 @@ def test_dense_rejects_bad_input(ctx):
         assert size[0] == 50 and best == 0
     finally:
         G.close()
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("h,M,eps", [(2, 16, 0.5), (3, 24, 0.3), (2, 535, 0.5)])
+def test_dense_pruned_along_sampled_core(ctx, name, h, M, eps):
+    """The faster EstDense variant of Sec. 6 (nodes with c' < gamma k' removed
+    first): sums, sizes, kept mask and the densest round equal the oracle's,
+    exact and sampled, along the sampled core's order."""
+    rowptr, col = GRAPHS[name]()
+    n = rowptr.size - 1
+    core, rnd, _ = O.core_sampled(rowptr, col, O.ranks(n, 1), h, M)
+    rounds = int(rnd.max()) + 1
+    for exact in (True, False):
+        want_sum, want_size, want_keep = O.dense_curve_pruned(
+            rowptr, col, O.ranks(n, 7), h, M, exact, rnd, rounds, core, eps)
+        G = K.kh_graph_load_csr(ctx, rowptr, col)
+        try:
+            K.kh_set_h(G, h)
+            K.kh_set_sampling(G, seed=7, M=M)
+            got_sum, got_size, best, kept = K.kh_dense_pruned(G, exact, rnd, rounds, core, eps)
+            ro, _, _ = K.kh_peel_info(G, True)
+        finally:
+            G.close()
+        assert np.array_equal(kept, want_keep)
+        assert np.array_equal(got_size, want_size)
+        assert np.array_equal(got_sum, want_sum)
+        assert best == densest(want_sum, want_size)
+        assert (ro[kept == 0] == -1).all() and np.array_equal(ro[kept == 1], rnd[kept == 1])

@@ -6,7 +6,7 @@ which runs only the oracle (exact h-degrees, Sec. 2; fixed-level counts, Alg. 1
 with the level forced; estimates through Prop. 3.1 / Alg. 2 levels and Alg. 1).
 Both sides hash the raw little-endian bytes of the same dtype and shape, so an
 equal digest is an element-by-element equality of the whole vector.  When a
-digest differs and the oracle's vector is cached locally (tests/golden/_cache),
+digest differs and the oracle's vector is cached locally (KH_ORACLE_CACHE, else tests/golden/_cache),
 the first differing nodes are reported.
 """
 import hashlib
@@ -21,7 +21,7 @@ from paper_2112_06154_gb300 import khcore as K
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 DIGESTS = os.path.join(HERE, "golden", "fullsize_sha256.txt")
-CACHE = os.path.join(HERE, "golden", "_cache")
+CACHE = os.environ.get("KH_ORACLE_CACHE") or os.path.join(HERE, "golden", "_cache")
 
 
 def read_digests():

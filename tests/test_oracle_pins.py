@@ -453,6 +453,35 @@ def test_dense_curve_sampled_is_sum_of_definition_estimates():
         assert size[q] == n - q
 
 
+@pytest.mark.parametrize("h,M,eps", [(1, 4, 0.5), (2, 5, 0.3), (2, 3, 0.5), (3, 6, 0.2)])
+def test_dense_curve_pruned(h, M, eps):
+    """The faster EstDense variant (Sec. 6): nodes with c'(v) < gamma k' are
+    dropped first.  Kept set by its definition; exact sums are twice the
+    brute-force pair counts inside each pruned candidate; along Core's own
+    order the pruned candidates are the unpruned suffixes from the first
+    round whose nodes all pass (c' only grows along Core's order)."""
+    rowptr, col = gg.chung_lu(120, 6, 2.3, 25, 13 + h)
+    n = rowptr.size - 1
+    r = O.ranks(n, 4)
+    core, rnd, _ = O.core_sampled(rowptr, col, r, h, M)
+    rounds = int(rnd.max()) + 1
+    gamma = (1 - eps) / (1 + eps)
+    for exact in (True, False):
+        total, size, keep = O.dense_curve_pruned(rowptr, col, r, h, M, exact, rnd, rounds, core, eps)
+        want_keep = core.astype(np.float64) >= gamma * float(core.max())
+        assert np.array_equal(keep.astype(bool), want_keep)
+        full, fsize = O.dense_curve(rowptr, col, r, h, M, exact, rnd, rounds)
+        q0 = int(rnd[want_keep].min())
+        assert (rnd[~want_keep] < q0).all()
+        assert np.array_equal(total[q0:], full[q0:]) and np.array_equal(size[q0:], fsize[q0:])
+        assert (total[:q0] == full[q0]).all() and (size[:q0] == fsize[q0]).all()
+        if exact:
+            for q in range(rounds):
+                alive = (rnd >= q) & want_keep
+                assert size[q] == alive.sum()
+                assert total[q] == 2 * brute_pairs_within_h(rowptr, col, h, alive)
+
+
 def test_dense_curve_rejects_bad_schedules():
     rowptr, col = gg.erdos_renyi(10, 12, 1)
     with pytest.raises(Exception):
