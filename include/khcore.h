@@ -225,22 +225,25 @@ int kh_launch_count(kh_graph *g, int64_t *launches);
 /* Exact h-degrees without allocating (the paper has no counterpart: this is
  * a deployment variant of kh_hdegree_exact).  For callers that cannot
  * allocate device memory -- a server whose device memory is owned by a pool
- * sized once at start-up, code enqueueing work while its stream is being
- * captured into a CUDA graph (cudaMalloc is not allowed there), or a
- * latency-bound caller that must not wait on the allocator.
+ * sized once at start-up, or a latency-bound caller that must not wait on the
+ * allocator.
  * n, rowptr (int64[n+1]) and col (int32[rowptr[n]]) describe a graph that
- * kh_graph_load_csr would accept (it is not validated here); all three
- * arrays and deg (int32[n], out: deg[v] = |N(v; h, V)| - 1) are device
- * memory of the current device.  cuda_stream is a cudaStream_t or NULL
- * (legacy default stream); the call only enqueues work on it.
+ * kh_graph_load_csr would accept; it is not validated here, except that a
+ * column id outside [0, n) is skipped instead of being visited (the degrees
+ * are then meaningless; no error is reported).  All three arrays and deg
+ * (int32[n], out: deg[v] = |N(v; h, V)| - 1) are device memory of the current
+ * device.  cuda_stream is a cudaStream_t or NULL (legacy default stream); the
+ * call only enqueues work on it.
  * Scratch lives in one fixed 64 MiB device array inside the library, which
  * every GPU that loads the library holds until the process exits; no call
  * allocates or frees memory.  Limits: 1 <= h <= 16 and n <= 819200 (the
  * visited set lives in shared memory); larger n returns KH_EINVAL.
  * The first call on a device looks the array up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
- * Every call shares the one array, so calls that overlap on the GPU (on
- * different streams, or from different threads) race: serialise them. */
+ * that device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process: after a cudaDeviceReset the
+ * entry point must not be called again.  Every call shares the one array, so
+ * calls that overlap on the GPU (on different streams, or from different
+ * threads) race: serialise them. */
 int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col, int32_t h,
                              int32_t *deg, void *cuda_stream);
 

@@ -9,6 +9,7 @@
 // frontier is expanded warp-per-vertex; vertices of degree >= kHeavyDeg (and a
 // lone frontier vertex) are expanded by the whole CTA.  New vertices are
 // appended to the CTA's queue with one warp-aggregated atomic per warp step.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -148,6 +149,12 @@ __device__ __forceinline__ void visit(const BfsArgs& a, uint32_t* bm, int32_t* q
                                       int lane,
                                       int& my, int32_t base) {
     bool isnew = false;
+    // ALLALIVE (the allocation-free entry point, whose graph is not validated):
+    // an id outside [0, n) is skipped, never used as a bitmap index
+    if (ALLALIVE && valid && (uint32_t)u >= (uint32_t)a.n) {
+        valid = false;
+        atomicOr(a.err, kErrGraph);
+    }
     // seeded: removed nodes already have their bit set, no alive lookup needed;
     // ALLALIVE: the whole graph, no alive array at all
     if (valid && (SEEDED || ALLALIVE || a.alive[u] == 1)) {
@@ -652,9 +659,8 @@ void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStrea
 // Exact h-degrees without any allocation
 //
 // Some callers cannot allocate device memory: a serving process whose device
-// memory is carved up once at start-up by its own pool, code enqueueing work
-// while a stream is being captured into a CUDA graph (where cudaMalloc is not
-// allowed), or a real-time caller that must not block on the allocator.  This
+// memory is carved up once at start-up by its own pool, or a real-time caller
+// that must not block on the allocator.  This
 // variant of the BFS kernel runs on caller-owned inputs and outputs and keeps
 // its scratch (work counter and the per-CTA BFS queues) in one file-scope
 // device array of fixed size, which every GPU that loads the library holds
@@ -669,8 +675,9 @@ constexpr int64_t kNoAllocMaxN = (kSmemBitmapMax / 4) * 32;
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocScratchInts];
 // host-side: the device address of g_noalloc_scratch on each device, looked
-// up once per device (the symbol itself is only a host stand-in)
-int32_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// up once per device (the symbol itself is only a host stand-in); atomic, as
+// two host threads may make their first call on a device at the same time
+std::atomic<int32_t*> g_noalloc_addr[kNoAllocMaxDevices] = {};
 }  // namespace
 
 }  // namespace kh
@@ -688,16 +695,17 @@ extern "C" int kh_hdegree_exact_noalloc(int64_t n, const int64_t* rowptr, const 
         return KH_ECUDA;
     }
     if (dev < 0 || dev >= kNoAllocMaxDevices) return KH_EINVAL;
-    if (!g_noalloc_addr[dev]) {
+    int32_t* base = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!base) {
         // first call on this device (with it current): find the array's address
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return KH_ECUDA;
         }
-        g_noalloc_addr[dev] = (int32_t*)p;
+        base = (int32_t*)p;  // every thread finds the same address
+        g_noalloc_addr[dev].store(base, std::memory_order_release);
     }
-    int32_t* base = g_noalloc_addr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int sm = 0;
     if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

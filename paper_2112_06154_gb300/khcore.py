@@ -409,9 +409,24 @@ def kh_get_variant(g: Graph, op: int = KH_OP_HDEG2):
 def kh_hdegree_exact_noalloc(rowptr, col, h: int, deg, stream=None) -> int:
     """Allocation-free exact h-degrees on device tensors (see include/khcore.h).
 
-    rowptr int64[n+1], col int32[nnz] and deg int32[n] are CUDA tensors of
-    the current device; returns the C return code (0 on success)."""
+    rowptr int64[n+1], col int32[nnz] and deg int32[n] are contiguous 1-D CUDA
+    tensors of the current device (KhError KH_EINVAL otherwise: the library
+    reads them as such without checking); returns the C return code (0 on
+    success)."""
+    import torch
+    for name, t, dt in (("rowptr", rowptr, torch.int64), ("col", col, torch.int32),
+                        ("deg", deg, torch.int32)):
+        if not _is_torch(t) or not t.is_cuda or t.dim() != 1 or not t.is_contiguous():
+            raise KhError(KH_EINVAL, f"{name} must be a contiguous 1-D CUDA tensor")
+        if t.dtype != dt:
+            raise KhError(KH_EINVAL, f"{name} must be {dt}")
+        if t.device.index != torch.cuda.current_device():
+            raise KhError(KH_EINVAL, f"{name} must be on the current device")
     n = int(rowptr.shape[0]) - 1
+    if n < 0 or deg.numel() != n:
+        raise KhError(KH_EINVAL, "deg needs one entry per node (rowptr has n + 1)")
+    if n > 0 and int(rowptr[-1].item()) != col.numel():
+        raise KhError(KH_EGRAPH, "rowptr[-1] must equal the length of col")
     s = None
     if stream is not None:
         s = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
