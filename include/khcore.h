@@ -267,6 +267,14 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
 #define KH_VAR_AUTO 0
 #define KH_VAR_CTA 1
 #define KH_VAR_SLICED 2
+/* KH_OP_PEEL_COMPACT: the peels (kh_core_*, kh_dense*) switch, each time the
+ * alive node count has halved, to a CSR that keeps only the neighbours alive
+ * at that moment (node ids unchanged; results unchanged).  KH_VAR_AUTO: for
+ * graphs of at least 65536 nodes; KH_COMPACT_OFF: never; KH_COMPACT_ALWAYS:
+ * at any size.  slices and threads are ignored. */
+#define KH_OP_PEEL_COMPACT 1
+#define KH_COMPACT_OFF 1
+#define KH_COMPACT_ALWAYS 2
 int kh_set_variant(kh_graph *g, int32_t op, int32_t variant, int32_t slices, int32_t threads);
 int kh_get_variant(kh_graph *g, int32_t op, int32_t *variant, int32_t *slices, int32_t *threads,
                    double *tuned_ms);

@@ -250,10 +250,20 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.degX);
     dfree(&g.lb64);
     dfree(&g.order2);
+    for (int b = 0; b < 2; ++b) {
+        dfree(&g.cp_row[b]);
+        dfree(&g.cp_col[b]);
+        dfree(&g.cp_list[b]);
+        g.cp_col_cap[b] = 0;
+    }
+    dfree(&g.cp_tmp);
+    dfree(&g.cp_sums);
     dfree(&g.part_keys);
     dfree(&g.part_size);
     dfree(&g.part_t);
     dfree(&g.part_done);
+    dfree(&g.part_stop);
+    dfree(&g.part_lb);
     dfree(&g.split_first);
     dfree(&g.sub_v);
     dfree(&g.sub_j);

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
             unsigned long long T = ~0ull;
             if (a.stop_c) {
                 const int g = a.gid ? a.gid[v] : 0;
-                T = a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g];
+                T = stop_level(a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g]);
             }
             s_T = T;
             bm[(v - base) >> 5] |= 1u << ((v - base) & 31);

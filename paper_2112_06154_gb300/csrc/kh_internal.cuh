@@ -99,6 +99,17 @@ struct DevState {
 
 struct Graph;
 
+// The lazy refine decides whether d(v) <= T = max(c, U) and may stop once a
+// partial value (a lower bound of d(v)) exceeds it.  It runs on until the
+// partial value exceeds kStopSlack * T instead: the node's new lower bound then
+// stays above the rising threshold for longer, so a node whose value is far
+// above T is refined O(log) times instead of once per round (any lower bound
+// above T gives the same removal decision).
+constexpr unsigned long long kStopSlack = 2;
+__host__ __device__ __forceinline__ unsigned long long stop_level(unsigned long long T) {
+    return T >= (~0ull) / kStopSlack ? ~0ull : T * kStopSlack;
+}
+
 // A launch layout of the whole-graph exact 2-degree pass (kh_tune.cu):
 // variant KH_VAR_CTA or KH_VAR_SLICED (KH_VAR_AUTO: not chosen yet), the
 // sliced kernel's slice count and CTA size, and the sample time it took.
@@ -290,7 +301,7 @@ struct Graph {
     std::vector<float>* prof_trace[kProfKinds];  // per-bracket ms, in launch order
     // cached CUDA graph of a batch of peeling rounds
     cudaGraphExec_t round_exec;
-    int round_exec_key[8];
+    int round_exec_key[10];
     int64_t round_exec_kernels;  // kernels in one replay of round_exec
     // kernels launched on behalf of this graph (graph replays count their nodes)
     int64_t launches;
@@ -302,10 +313,28 @@ struct Graph {
     int32_t *part_size;
     uint8_t *part_t;
     int32_t *part_done;
+    int32_t *part_stop;
+    unsigned long long *part_lb;
     int32_t *split_first;
     int32_t *sub_v;
     int32_t *sub_j;
     bool split_planned;     // part_cap computed for this graph
+    // the peel's view of the graph (kh_peel.cu): rowptr/col above are switched
+    // to a compacted CSR of the nodes alive at the last compaction, and the
+    // whole-node scans run over vlist (vcount nodes; nullptr: all n); the
+    // graph's own arrays are kept in orig_* and restored when the peel ends
+    int64_t *orig_rowptr;
+    int32_t *orig_col;
+    const int32_t *vlist;
+    int64_t vcount;
+    int compact_mode;       // KH_VAR_AUTO, KH_COMPACT_OFF or KH_COMPACT_ALWAYS
+    int cp_cur;             // buffer set in use (0 or 1)
+    int64_t *cp_row[2];
+    int32_t *cp_col[2];
+    int64_t cp_col_cap[2];
+    int32_t *cp_list[2];
+    int64_t *cp_tmp;        // counts and flags, 2 (n + 1)
+    int64_t *cp_sums;       // scan tile totals
     // sliced 2-degree kernel: sources longest first (non-isolated nodes only)
     int32_t *order2;
     int64_t nsrc2;

@@ -86,13 +86,14 @@ __device__ __forceinline__ unsigned long long umin(unsigned long long a, unsigne
 // first, so most nodes need none).
 template <typename T>
 __global__ void k_min_alive(const uint8_t* __restrict__ alive, const uint8_t* __restrict__ fresh,
-                            const T* __restrict__ d, int64_t n, DevState* st,
-                            unsigned long long* mu, unsigned long long* mn,
+                            const T* __restrict__ d, int64_t n, const int32_t* __restrict__ vl,
+                            DevState* st, unsigned long long* mu, unsigned long long* mn,
                             const int32_t* __restrict__ gid) {
     if (st->n_alive == 0) return;
     unsigned long long m = ~0ull, mf = ~0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t v = vl ? vl[i] : i;
         if (alive[v] == 1) {
             const unsigned long long x = (unsigned long long)d[v];
             const bool fr = fresh[v] != 0;
@@ -105,6 +106,7 @@ __global__ void k_min_alive(const uint8_t* __restrict__ alive, const uint8_t* __
                 if (fr) mf = umin(mf, x);
             }
         }
+    }
     if (gid) return;
     for (int off = 16; off > 0; off >>= 1) {
         m = umin(m, __shfl_down_sync(kFull, m, off));
@@ -160,14 +162,16 @@ __global__ void k_min_lb(const uint8_t* __restrict__ alive, const uint8_t* __res
 // Stale nodes with lb <= T = max(c, U) join the refine list and become fresh
 // (their value is recomputed right after, before anything reads it).
 __global__ void k_collect(const uint8_t* __restrict__ alive, uint8_t* __restrict__ fresh, int64_t n,
-                          LbArgs a, DevState* st, PeelState p, int32_t* __restrict__ out) {
+                          const int32_t* __restrict__ vl, LbArgs a, DevState* st, PeelState p,
+                          int32_t* __restrict__ out) {
     if (st->n_alive == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
         bool due = false;
-        if (v < n && alive[v] == 1 && !fresh[v]) {
+        const int64_t v = i < n ? (vl ? vl[i] : i) : 0;
+        if (i < n && alive[v] == 1 && !fresh[v]) {
             const int g = graph_of(p, v);
             const unsigned long long T = p.c[g] > p.mu[g] ? p.c[g] : p.mu[g];
             due = lower_bound(a, (int)v) <= T;
@@ -217,7 +221,8 @@ __global__ void k_init_keep(const uint8_t* __restrict__ keep, int64_t n, uint8_t
 
 template <typename T, typename C>
 __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
-                         DevState* st, PeelState p, C* __restrict__ core, int32_t* __restrict__ round_of,
+                         const int32_t* __restrict__ vl, DevState* st, PeelState p,
+                         C* __restrict__ core, int32_t* __restrict__ round_of,
                          int32_t* __restrict__ R, int32_t* __restrict__ seen) {
     if (st->n_alive == 0) return;
     const int round = st->round;
@@ -225,9 +230,10 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
     int keep = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
         bool rm = false;
-        if (v < n && alive[v] == 1) {
+        const int64_t v = i < n ? (vl ? vl[i] : i) : 0;
+        if (i < n && alive[v] == 1) {
             const int g = graph_of(p, v);
             const unsigned long long m = round_min(p, g);
             const unsigned long long c = p.c[g] > m ? p.c[g] : m;
@@ -258,8 +264,9 @@ __global__ void k_select(uint8_t* __restrict__ alive, const T* __restrict__ d, i
 // c in round `round + 1`.  Every block evaluates the condition; block 0
 // records it for the kernels that follow (they skip the refresh).
 template <typename C>
-__global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* st, PeelState p,
-                              C* __restrict__ core, int32_t* __restrict__ round_of) {
+__global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, const int32_t* __restrict__ vl,
+                              DevState* st, PeelState p, C* __restrict__ core,
+                              int32_t* __restrict__ round_of) {
     if (st->n_alive == 0) return;
     // single graphs only (a batch has no global early stop)
     const unsigned long long m = round_min(p, 0);
@@ -270,25 +277,29 @@ __global__ void k_assign_rest(uint8_t* __restrict__ alive, int64_t n, DevState* 
     if (!early) return;
     const int round = st->round + 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t v = vl ? vl[i] : i;
         if (alive[v] == 1) {
             core[v] = (C)c;
             round_of[v] = round;
             alive[v] = 0;
         }
+    }
 }
 
 // Batches: the early stop of each graph on its own (c_g >= |X_g| - 1 after
 // this round's removal).  Finished graphs' nodes leave at once, so the
 // refresh that follows never reaches them.
 template <typename C>
-__global__ void k_assign_rest_batch(uint8_t* __restrict__ alive, int64_t n, DevState* st,
-                                    PeelState p, C* __restrict__ core, int32_t* __restrict__ round_of) {
+__global__ void k_assign_rest_batch(uint8_t* __restrict__ alive, int64_t n,
+                                    const int32_t* __restrict__ vl, DevState* st, PeelState p,
+                                    C* __restrict__ core, int32_t* __restrict__ round_of) {
     if (st->n_alive == 0) return;
     const int round = st->round + 1;
     int gone = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t v = vl ? vl[i] : i;
         if (alive[v] == 1) {
             const int g = p.gid[v];
             const unsigned long long m = round_min(p, g);
@@ -301,6 +312,7 @@ __global__ void k_assign_rest_batch(uint8_t* __restrict__ alive, int64_t n, DevS
                 ++gone;
             }
         }
+    }
     for (int off = 16; off > 0; off >>= 1) gone += __shfl_down_sync(kFull, gone, off);
     if ((threadIdx.x & 31) == 0 && gone) atomicSub(&st->n_alive_next, gone);
 }
@@ -351,15 +363,17 @@ __global__ void k_finish(uint8_t* __restrict__ alive, const int32_t* __restrict_
 // current; its sum of d goes to dsum[round].
 template <typename T>
 __global__ void k_dense_sum(const uint8_t* __restrict__ alive, const T* __restrict__ d, int64_t n,
-                            const DevState* __restrict__ st, unsigned long long* __restrict__ dsum,
-                            int64_t cap) {
+                            const int32_t* __restrict__ vl, const DevState* __restrict__ st,
+                            unsigned long long* __restrict__ dsum, int64_t cap) {
     if (st->n_alive == 0) return;
     const int round = st->round;
     if (round >= cap) return;
     unsigned long long s = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t v = vl ? vl[i] : i;
         if (alive[v] == 1) s += (unsigned long long)d[v];
+    }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(kFull, s, off);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dsum + round, s);
 }
@@ -367,17 +381,19 @@ __global__ void k_dense_sum(const uint8_t* __restrict__ alive, const T* __restri
 // EstDense: the nodes whose scheduled round has come leave (the removal order
 // is given, not chosen by d).
 __global__ void k_select_sched(uint8_t* __restrict__ alive, const int32_t* __restrict__ sched,
-                               int64_t n, DevState* st, int32_t* __restrict__ R,
-                               int32_t* __restrict__ seen, int32_t* __restrict__ round_of) {
+                               int64_t n, const int32_t* __restrict__ vl, DevState* st,
+                               int32_t* __restrict__ R, int32_t* __restrict__ seen,
+                               int32_t* __restrict__ round_of) {
     if (st->n_alive == 0) return;
     const int round = st->round;
     const int lane = threadIdx.x & 31;
     int keep = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nround = (n + 31) & ~(int64_t)31;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
         bool rm = false;
-        if (v < n && alive[v] == 1) {
+        const int64_t v = i < n ? (vl ? vl[i] : i) : 0;
+        if (i < n && alive[v] == 1) {
             if (sched[v] <= round) {
                 rm = true;
                 round_of[v] = round;
@@ -397,8 +413,196 @@ __global__ void k_select_sched(uint8_t* __restrict__ alive, const int32_t* __res
     if (lane == 0 && keep) atomicAdd(&st->n_alive_next, keep);
 }
 
+// ---- compaction of the peel's graph ----------------------------------------
+// As nodes leave, rows still list them.  Once the alive count has halved since
+// the last compaction, the peel switches to a CSR that keeps, for every node,
+// only the neighbours alive at that moment, and to the list of those nodes for
+// its whole-node scans.  Every peel kernel filters rows by alive (1: alive, 2:
+// removed this round, 0: removed earlier) and only ever needs neighbours with
+// alive != 0, all of which were alive at the last compaction, so the kept rows
+// serve the rest of the peel unchanged; node ids stay the same.
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+// Exclusive scan of one tile of `in` into `out`; the tile's total to sums[tile].
+__global__ void k_scan_tiles(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out,
+                             int64_t* __restrict__ sums) {
+    __shared__ int64_t s_w[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t x[kScanPer];
+    int64_t t = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        x[j] = base + j < n ? in[base + j] : 0;
+        t += x[j];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t inc = t;  // inclusive warp scan of the thread totals
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    int64_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_w[w];
+    int64_t run = before + inc - t;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+        if (base + j < n) out[base + j] = run;
+        run += x[j];
+    }
+    if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = before + inc;
+}
+
+// Exclusive scan of the tile totals (one block, in chunks with a carry).
+__global__ void k_scan_sums(int64_t* __restrict__ sums, int64_t tiles) {
+    __shared__ int64_t s_w[kScanThreads / 32];
+    __shared__ int64_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c0 = 0; c0 < tiles; c0 += kScanThreads) {
+        const int64_t i = c0 + threadIdx.x;
+        const int64_t x = i < tiles ? sums[i] : 0;
+        int64_t inc = x;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, inc, off);
+            if (lane >= off) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        int64_t before = s_carry;
+        for (int w = 0; w < warp; ++w) before += s_w[w];
+        if (i < tiles) sums[i] = before + inc - x;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) s_carry = before + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ sums) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] += sums[i / kScanTile];
+}
+
+// Per listed alive node: its alive neighbours and itself (flag), warp per node.
+__global__ void k_compact_count(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const uint8_t* __restrict__ alive, const int32_t* __restrict__ vl,
+                                int64_t vn, int64_t* __restrict__ cnt, int64_t* __restrict__ flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < vn; i += nw) {
+        const int64_t v = vl ? vl[i] : i;
+        if (alive[v] != 1) continue;
+        int64_t c = 0;
+        for (int64_t k = rowptr[v] + lane; k < rowptr[v + 1]; k += 32) c += alive[col[k]] == 1;
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(kFull, c, off);
+        if (lane == 0) {
+            cnt[v] = c;
+            flag[v] = 1;
+        }
+    }
+}
+
+// Write each listed alive node's alive neighbours (in row order) and the node
+// itself into the new CSR and list.
+__global__ void k_compact_fill(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const uint8_t* __restrict__ alive, const int32_t* __restrict__ vl,
+                               int64_t vn, const int64_t* __restrict__ nrow,
+                               const int64_t* __restrict__ pos, int32_t* __restrict__ ncol,
+                               int32_t* __restrict__ nlist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < vn; i += nw) {
+        const int64_t v = vl ? vl[i] : i;
+        if (alive[v] != 1) continue;
+        int64_t out = nrow[v];
+        for (int64_t k0 = rowptr[v]; k0 < rowptr[v + 1]; k0 += 32) {
+            const int64_t k = k0 + lane;
+            int32_t u = 0;
+            bool keep = false;
+            if (k < rowptr[v + 1]) {
+                u = col[k];
+                keep = alive[u] == 1;
+            }
+            const uint32_t m = __ballot_sync(kFull, keep);
+            if (keep) ncol[out + __popc(m & ((1u << lane) - 1u))] = u;
+            out += __popc(m);
+        }
+        if (lane == 0) nlist[pos[v]] = (int32_t)v;
+    }
+}
+
+// Exclusive scan of n values (n + 1 outputs would need in[n] = 0).
+int scan_i64(Graph& g, const int64_t* in, int64_t n, int64_t* out, int64_t* sums, cudaStream_t s) {
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 0) return KH_OK;
+    k_scan_tiles<<<(int)tiles, kScanThreads, 0, s>>>(in, n, out, sums);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, tiles);
+    k_scan_add<<<g.ctx->sm_count * 4, 256, 0, s>>>(out, n, sums);
+    count_launch(g, 3);
+    return KH_OK;
+}
+
+// Rebuild the peel's CSR and node list from the alive nodes (between rounds).
+int compact_peel(Graph& g, cudaStream_t s) {
+    const size_t n1 = (size_t)g.n + 1;
+    int rc;
+    if (!g.cp_tmp) {
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.cp_tmp, sizeof(int64_t) * 2 * n1, "compaction counts")))
+            return rc;
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.cp_sums,
+                              sizeof(int64_t) * (2 * (n1 / kScanTile) + 4), "compaction sums")))
+            return rc;
+    }
+    const int nb = g.cp_cur ^ 1;  // the buffer set not in use
+    if (!g.cp_row[nb]) {
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.cp_row[nb], sizeof(int64_t) * n1, "compacted rowptr")))
+            return rc;
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.cp_list[nb], sizeof(int32_t) * n1, "compacted list")))
+            return rc;
+    }
+    int64_t* cnt = g.cp_tmp;
+    int64_t* flag = g.cp_tmp + n1;
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.cp_tmp, 0, sizeof(int64_t) * 2 * n1, s));
+    const int grid = g.ctx->sm_count * 8;
+    k_compact_count<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.vlist, g.vcount, cnt, flag);
+    count_launch(g, 1);
+    int64_t* pos = g.cp_tmp + n1;  // scanned in place over the flags
+    if ((rc = scan_i64(g, cnt, (int64_t)n1, g.cp_row[nb], g.cp_sums, s))) return rc;
+    if ((rc = scan_i64(g, flag, (int64_t)n1, pos, g.cp_sums + (n1 / kScanTile) + 2, s))) return rc;
+    int64_t tot[2] = {0, 0};
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&tot[0], g.cp_row[nb] + g.n, sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, s));
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(&tot[1], pos + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
+    if (g.cp_col_cap[nb] < tot[0]) {
+        if (g.cp_col[nb]) cudaFree(g.cp_col[nb]);
+        g.cp_col[nb] = nullptr;
+        g.cp_col_cap[nb] = 0;
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.cp_col[nb], sizeof(int32_t) * (size_t)(tot[0] > 0 ? tot[0] : 1),
+                              "compacted col")))
+            return rc;
+        g.cp_col_cap[nb] = tot[0];
+    }
+    k_compact_fill<<<grid, 256, 0, s>>>(g.rowptr, g.col, g.alive, g.vlist, g.vcount, g.cp_row[nb], pos,
+                                        g.cp_col[nb], g.cp_list[nb]);
+    count_launch(g, 1);
+    KH_CUDA_TRY(g.ctx, cudaGetLastError());
+    g.rowptr = g.cp_row[nb];
+    g.col = g.cp_col[nb];
+    g.vlist = g.cp_list[nb];
+    g.vcount = tot[1];
+    g.cp_cur = nb;
+    return KH_OK;
+}
+
 int peel_grid(const Graph& g) {
-    int64_t grid = (g.n + kPeelThreads - 1) / kPeelThreads;
+    int64_t grid = (g.vcount + kPeelThreads - 1) / kPeelThreads;
     const int64_t gmax = (int64_t)g.ctx->sm_count * 4;
     if (grid > gmax) grid = gmax;
     return (int)(grid < 1 ? 1 : grid);
@@ -428,7 +632,8 @@ int refine(Graph& g, bool sampled, cudaStream_t s) {
     const int grid = peel_grid(g);
     const LbArgs la = lb_args(g);
     prof_begin(g, kProfPeel, s);
-    k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.n, la, g.state, peel_state(g), g.listB);
+    k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.vcount, g.vlist, la, g.state,
+                                            peel_state(g), g.listB);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s, 2);
@@ -517,13 +722,13 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
         if (rc) return rc;
         prof_begin(g, kProfPeel, s);
         if (sampled)
-            k_dense_sum<unsigned long long><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d64, g.n, g.state,
-                                                                         g.dsum, g.n + 1);
+            k_dense_sum<unsigned long long><<<grid, kPeelThreads, 0, s>>>(
+                g.alive, g.d64, g.vcount, g.vlist, g.state, g.dsum, g.n + 1);
         else
-            k_dense_sum<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.n, g.state, g.dsum,
-                                                               g.n + 1);
-        k_select_sched<<<grid, kPeelThreads, 0, s>>>(g.alive, g.sched, g.n, g.state, g.listR, g.seen,
-                                                     g.round_of);
+            k_dense_sum<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.d32, g.vcount, g.vlist,
+                                                               g.state, g.dsum, g.n + 1);
+        k_select_sched<<<grid, kPeelThreads, 0, s>>>(g.alive, g.sched, g.vcount, g.vlist, g.state,
+                                                     g.listR, g.seen, g.round_of);
         count_launch(g, 2);
         prof_end(g, kProfPeel, s);
         return refresh_and_finish(g, sampled, s);
@@ -533,10 +738,10 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     prof_begin(g, kProfPeel, s);
     if (sampled)
         k_min_alive<unsigned long long><<<grid, kPeelThreads, 0, s>>>(
-            g.alive, g.fresh, g.d64, g.n, g.state, g.pmu, g.pmn, g.gid);
+            g.alive, g.fresh, g.d64, g.vcount, g.vlist, g.state, g.pmu, g.pmn, g.gid);
     else
-        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.d32, g.n, g.state,
-                                                           g.pmu, g.pmn, g.gid);
+        k_min_alive<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.d32, g.vcount, g.vlist,
+                                                           g.state, g.pmu, g.pmn, g.gid);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     rc = refine(g, sampled, s);
@@ -545,18 +750,19 @@ int launch_round(Graph& g, bool sampled, cudaStream_t s) {
     const PeelState ps = peel_state(g);
     if (sampled) {
         k_select<unsigned long long, unsigned long long><<<grid, kPeelThreads, 0, s>>>(
-            g.alive, g.d64, g.n, g.state, ps, g.core64, g.round_of, g.listR, g.seen);
+            g.alive, g.d64, g.vcount, g.vlist, g.state, ps, g.core64, g.round_of, g.listR, g.seen);
         count_launch(g, 1);
     } else {
         k_select<int32_t, int32_t><<<grid, kPeelThreads, 0, s>>>(
-            g.alive, g.d32, g.n, g.state, ps, g.core32, g.round_of, g.listR, g.seen);
+            g.alive, g.d32, g.vcount, g.vlist, g.state, ps, g.core32, g.round_of, g.listR, g.seen);
         count_launch(g, 1);
         if (!g.gid)  // the early stop of Sec. 5
-            k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, ps, g.core32,
-                                                                 g.round_of);
+            k_assign_rest<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.vcount, g.vlist, g.state,
+                                                                 ps, g.core32, g.round_of);
         else  // the same, graph by graph
-            k_assign_rest_batch<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.n, g.state, ps,
-                                                                       g.core32, g.round_of);
+            k_assign_rest_batch<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.vcount, g.vlist,
+                                                                       g.state, ps, g.core32,
+                                                                       g.round_of);
         count_launch(g, 1);
     }
     prof_end(g, kProfPeel, s);
@@ -572,9 +778,10 @@ int check_state_err(Graph& g, const DevState& hs) {
 // Capture kRoundsPerGraph rounds into an executable graph (cached per shape).
 int round_graph(Graph& g, bool sampled, cudaStream_t s, cudaGraphExec_t* out) {
     // everything a captured launch bakes in: mode, h, M, slot size, scratch, batch tables
-    const int key[8] = {(sampled ? 1 : 0) | (g.dense ? 2 : 0), g.h, (int)g.M, (int)g.cap, (int)g.scratch_ctas,
-                        (int)(reinterpret_cast<uintptr_t>(g.hv) >> 4),
-                        (int)(reinterpret_cast<uintptr_t>(g.Mv) >> 4), g.hmin};
+    const int key[10] = {(sampled ? 1 : 0) | (g.dense ? 2 : 0), g.h, (int)g.M, (int)g.cap,
+                         (int)g.scratch_ctas, (int)(reinterpret_cast<uintptr_t>(g.hv) >> 4),
+                         (int)(reinterpret_cast<uintptr_t>(g.Mv) >> 4), g.hmin,
+                         (int)(reinterpret_cast<uintptr_t>(g.rowptr) >> 4), (int)g.vcount};
     if (g.round_exec && memcmp(key, g.round_exec_key, sizeof(key)) == 0) {
         *out = g.round_exec;
         return KH_OK;
@@ -627,9 +834,29 @@ int run_estimate_all(Graph& g) {
     return KH_OK;
 }
 
+// The peel's CSR and node list are the graph's own outside a peel.
+struct PeelView {
+    Graph& g;
+    explicit PeelView(Graph& gg) : g(gg) {
+        g.orig_rowptr = g.rowptr;
+        g.orig_col = g.col;
+        g.vlist = nullptr;
+        g.vcount = g.n;
+    }
+    ~PeelView() {
+        g.rowptr = g.orig_rowptr;
+        g.col = g.orig_col;
+        g.vlist = nullptr;
+        g.vcount = g.n;
+    }
+};
+
+constexpr int64_t kCompactMinAlive = 65536;  // automatic compaction only for larger graphs
+
 int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, bool out_dev) {
     (void)round_of_host;
     cudaStream_t s = g.ctx->stream;
+    PeelView view(g);
     int rc = ensure_work(g);
     if (rc) return rc;
     if (sampled) {
@@ -682,6 +909,7 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
         rc = round_graph(g, sampled, s, &exec);
         if (rc) return rc;
     }
+    int64_t compact_at = g.start_keep ? g.start_alive : g.n;  // alive count at the last compaction
     for (;;) {
         NvtxRange nvtx_range(use_graph ? "peel rounds (graph replay)" : "peel round");
         if (use_graph) {
@@ -699,6 +927,18 @@ int run_core(Graph& g, bool sampled, void* out_core, int32_t* round_of_host, boo
         rc = check_state_err(g, hs);
         if (rc) return rc;
         if (hs.n_alive == 0) break;
+        const bool may = g.compact_mode == KH_COMPACT_ALWAYS ||
+                         (g.compact_mode == KH_VAR_AUTO && compact_at >= kCompactMinAlive);
+        if (may && 2 * (int64_t)hs.n_alive <= compact_at) {
+            NvtxRange nvtx_compact("peel compaction");
+            rc = compact_peel(g, s);
+            if (rc) return rc;
+            compact_at = hs.n_alive;
+            if (use_graph) {
+                rc = round_graph(g, sampled, s, &exec);  // the launches changed: capture again
+                if (rc) return rc;
+            }
+        }
         if (launches > g.n + 2 + kRoundsPerGraph)
             return set_error(g.ctx, KH_ETIMEOUT, "peeling did not finish within n+1 rounds");
     }

@@ -85,6 +85,8 @@ struct LevelArgs {
     int32_t* part_size;
     uint8_t* part_t;
     int32_t* part_done;
+    int32_t* part_stop;             // per split node: some part stopped early (refine)
+    unsigned long long* part_lb;    // per split node: the largest partial estimate above T
     int32_t* split_first;
     int32_t* sub_v;
     int32_t* sub_j;
@@ -355,6 +357,11 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
     }
 }
 
+// A flag another CTA of this launch may set (read past the L1 cache).
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    return *(volatile const int32_t*)p;
+}
+
 // Insert `key` into the shared hash set; returns its slot if it was not
 // there, -1 if it was (or the probe limit was reached).
 __device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, int* err) {
@@ -476,9 +483,9 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 s_vin = 0;
                 s_exit = 0;
                 unsigned long long T = ~0ull;
-                if (a.stop_c && nl.last && mode == 0) {
+                if (a.stop_c && nl.last && mode != 2) {
                     const int g = a.gid ? a.gid[v] : 0;
-                    T = a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g];
+                    T = stop_level(a.stop_c[g] > a.stop_mu[g] ? a.stop_c[g] : a.stop_mu[g]);
                 }
                 s_T = T;
             }
@@ -676,6 +683,10 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                             s_exit = 1;
                             s_part = pe;
                         }
+                        // a part stops too once another part of the node has
+                        // shown d(v) > T
+                        if (mode == 1 && lane == 0 && !s_exit && ld_acquire(a.part_stop + first))
+                            s_exit = 2;
                     }
                     if (lane == 0) {
                         const int told = s_t;
@@ -717,20 +728,30 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 // d(v) > T: v stays stale, its lower bound raised to the partial estimate
                 const int nu = min(s_nused, hcap);
                 for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
-                if (tid == 0) {
-                    a.lb[v] = s_part;
-                    a.fresh[v] = 0;
-                    atomicAdd(a.stopped, 1ull);  // a lower bound only: not an update
-                    my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
+                if (mode == 0) {
+                    if (tid == 0) {
+                        a.lb[v] = s_part;
+                        a.fresh[v] = 0;
+                        atomicAdd(a.stopped, 1ull);  // a lower bound only: not an update
+                        my_bytes += 8ull + 10ull * (unsigned long long)deg + 9ull;
+                    }
+                    break;
                 }
-                break;
+                // a part: its partial set (a sub-multiset of N(v; h) led by v)
+                // already estimates above T; the node's last part finishes it
+                if (tid == 0) {
+                    if (s_exit == 1) atomicMax(a.part_lb + first, s_part);
+                    a.part_stop[first] = 1;
+                }
             }
             const int kappa = s_t;
             const int nu = min(s_nused, hcap);
             int S = 0;
             for (int j = kappa; j < 32; ++j) S += s_hist[j];
             __syncthreads();
-            if (mode == 1) {
+            if (mode == 1 && stopped) {
+                if (tid == 0) my_bytes += 10ull * (unsigned long long)L;
+            } else if (mode == 1) {
                 // this part's trimmed set, grouped by rank (highest first), and its level
                 if (tid < 32) {
                     int above = 0;
@@ -755,12 +776,26 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                     a.part_t[first + part] = (uint8_t)kappa;
                     my_bytes += 10ull * (unsigned long long)L;
                 }
+            }
+            if (mode == 1) {
                 __threadfence();
                 __syncthreads();
                 if (tid == 0) s_last = atomicAdd(a.part_done + first, 1) == nparts - 1;
                 __syncthreads();
                 if (!s_last) break;
                 __threadfence();  // the other parts' sets are visible from here on
+                if (__ldcg(a.part_stop + first)) {
+                    // some part showed d(v) > T: v stays stale with that lower bound
+                    if (tid == 0) {
+                        a.lb[v] = __ldcg(a.part_lb + first);
+                        a.fresh[v] = 0;
+                        atomicAdd(a.stopped, 1ull);
+                        a.part_stop[first] = 0;
+                        a.part_lb[first] = 0;
+                        a.part_done[first] = 0;
+                    }
+                    break;
+                }
                 mode = 2;
                 continue;
             }
@@ -1049,6 +1084,17 @@ int ensure_split(Graph& g) {
             return rc;
         KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.part_done, 0, sizeof(int32_t) * pc, s));
     }
+    if (!g.part_stop) {
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.part_stop, sizeof(int32_t) * pc, "split stop flags")))
+            return rc;
+        KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.part_stop, 0, sizeof(int32_t) * pc, s));
+    }
+    if (!g.part_lb) {
+        if ((rc = alloc_bytes(g.ctx, (void**)&g.part_lb, sizeof(unsigned long long) * pc,
+                              "split lower bounds")))
+            return rc;
+        KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.part_lb, 0, sizeof(unsigned long long) * pc, s));
+    }
     if (!g.part_size && (rc = alloc_bytes(g.ctx, (void**)&g.part_size, sizeof(int32_t) * pc, "split part sizes")))
         return rc;
     if (!g.part_t && (rc = alloc_bytes(g.ctx, (void**)&g.part_t, pc, "split part levels"))) return rc;
@@ -1131,6 +1177,8 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.part_size = g.part_size;
     a.part_t = g.part_t;
     a.part_done = g.part_done;
+    a.part_stop = g.part_stop;
+    a.part_lb = g.part_lb;
     a.split_first = g.split_first;
     a.sub_v = g.sub_v;
     a.sub_j = g.sub_j;

@@ -33,6 +33,9 @@ KH_OP_HDEG2 = 0
 KH_VAR_AUTO = 0
 KH_VAR_CTA = 1
 KH_VAR_SLICED = 2
+KH_OP_PEEL_COMPACT = 1
+KH_COMPACT_OFF = 1
+KH_COMPACT_ALWAYS = 2
 PROF_NAMES = ["bfs", "level1", "levelU", "frontier", "peel"]
 
 _ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",
@@ -393,7 +396,8 @@ def kh_launch_count(g: Graph) -> int:
 
 def kh_set_variant(g: Graph, variant: int, slices: int = 0, threads: int = 0,
                    op: int = KH_OP_HDEG2):
-    """Force the layout of the h = 2 exact-degree pass (KH_VAR_AUTO: the tuner's)."""
+    """Force the layout of the h = 2 exact-degree pass (KH_VAR_AUTO: the tuner's),
+    or (op=KH_OP_PEEL_COMPACT) the peel's compaction setting."""
     _check(load().kh_set_variant(g.handle, op, variant, slices, threads), g.ctx)
 
 
