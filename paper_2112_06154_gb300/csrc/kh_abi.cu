@@ -150,7 +150,10 @@ static int prof_collect(Graph& g) {
 int ensure_lists(Graph& g) {
     // lists for levels 1..hmax-1, sizes/levels for 1..hmax
     const int64_t need_keys = (int64_t)(g.hmax - 1) * g.n * g.cap;
-    if (g.keys && g.keys_levels * g.n * g.cap < need_keys) dfree(&g.keys);
+    if (g.keys && g.keys_levels * g.n * g.cap < need_keys) {
+        dfree(&g.keys);
+        dfree(&g.ltop);
+    }
     if (g.lsz && g.lvl_alloc < g.hmax) {
         dfree(&g.lsz);
         dfree(&g.lk);
@@ -158,6 +161,8 @@ int ensure_lists(Graph& g) {
     int rc;
     if (need_keys > 0) {
         if ((rc = dalloc(g.ctx, &g.keys, (size_t)need_keys, "sample lists"))) return rc;
+        if ((rc = dalloc(g.ctx, &g.ltop, (size_t)(g.hmax - 1) * (size_t)g.n, "list top ranks")))
+            return rc;
         g.keys_levels = g.hmax - 1;
     }
     if (!g.lsz) g.lvl_alloc = g.hmax;
@@ -208,6 +213,7 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.rank);
     dfree(&g.alive);
     dfree(&g.keys);
+    dfree(&g.ltop);
     dfree(&g.lsz);
     dfree(&g.lk);
     dfree(&g.d32);

@@ -227,6 +227,7 @@ struct Graph {
     uint8_t *rank;
     uint8_t *alive;
     uint32_t *keys;
+    uint8_t *ltop;          // highest rank of each stored list (levels 1..h-1)
     int64_t keys_levels;    // allocated levels in keys
     int32_t *lsz;
     uint8_t *lk;

@@ -51,6 +51,7 @@ struct LevelArgs {
     uint32_t* keys;            // level i lists at keys + (i-1) n cap
     int32_t* lsz;              // |B[v,i]| at lsz + (i-1) n
     uint8_t* lk;               // k[v,i] at lk + (i-1) n
+    uint8_t* ltop;             // highest rank in B[v,i] at ltop + (i-1) n, stored levels only
     unsigned long long* est;   // estimate (at a node's last level)
     const int32_t* worklist;
     const int* d_count;
@@ -112,8 +113,10 @@ struct NodeLevel {
     uint32_t* keys_out;
     const int32_t* lsz_in;
     const uint8_t* lk_in;
+    const uint8_t* ltop_in;
     int32_t* lsz_out;
     uint8_t* lk_out;
+    uint8_t* ltop_out;  // nullptr at a node's last level (no list is stored)
 };
 
 __device__ __forceinline__ NodeLevel node_level(const LevelArgs& a, int v) {
@@ -129,8 +132,10 @@ __device__ __forceinline__ NodeLevel node_level(const LevelArgs& a, int v) {
     nl.keys_out = (!nl.last && a.keys) ? a.keys + (size_t)(L - 1) * lc : nullptr;
     nl.lsz_in = L >= 2 ? a.lsz + (size_t)(L - 2) * nn : nullptr;
     nl.lk_in = L >= 2 ? a.lk + (size_t)(L - 2) * nn : nullptr;
+    nl.ltop_in = L >= 2 ? a.ltop + (size_t)(L - 2) * nn : nullptr;
     nl.lsz_out = a.lsz + (size_t)(L - 1) * nn;
     nl.lk_out = a.lk + (size_t)(L - 1) * nn;
+    nl.ltop_out = (!nl.last && a.ltop) ? a.ltop + (size_t)(L - 1) * nn : nullptr;
     return nl;
 }
 
@@ -228,6 +233,8 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
         const int kappa = over ? 32 - __clz(over) : 0;
         const int Sk = __shfl_sync(kFull, S, kappa & 31);
         const int Skap = kappa < 32 ? Sk : 0;
+        const uint32_t nz = __ballot_sync(kFull, S > 0);
+        const int top = nz ? 31 - __clz(nz) : 0;  // highest rank present
         if (lane == 0) my_bytes += level1_bytes(e - b, Skap, nl.last);
         if (nl.last) {
             if (lane == 0) {
@@ -270,6 +277,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
                 if (p < a.cap) out[p] = ((uint32_t)rv << kIdBits) | (uint32_t)v;
                 else atomicOr(a.err, kErrList);
             }
+            if (nl.ltop_out) nl.ltop_out[v] = (uint8_t)top;
             record_change(a, nl, v, Skap, kappa);
         }
         __syncwarp();
@@ -281,7 +289,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1(LevelArgs a) {
 // Level 1 for the nodes of degree > kL1Heavy deferred by k_level1: one CTA per node.
 __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
     __shared__ int s_hist[32];
-    __shared__ int s_kappa, s_S;
+    __shared__ int s_kappa, s_S, s_top;
     const int tid = threadIdx.x, lane = tid & 31;
     const int nh = *a.n_heavy;
     for (int idx = blockIdx.x; idx < nh; idx += gridDim.x) {
@@ -307,10 +315,12 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
             const int kappa = over ? 32 - __clz(over) : 0;
             const int Sk = __shfl_sync(kFull, S, kappa & 31);
             const int above = __shfl_down_sync(kFull, S, 1);
+            const uint32_t nz = __ballot_sync(kFull, S > 0);
             s_hist[lane] = lane < 31 ? above : 0;
             if (lane == 0) {
                 s_kappa = kappa;
                 s_S = kappa < 32 ? Sk : 0;
+                s_top = nz ? 31 - __clz(nz) : 0;
             }
         }
         __syncthreads();
@@ -349,6 +359,7 @@ __global__ void __launch_bounds__(kL1Threads) k_level1_heavy(LevelArgs a) {
                     if (p < a.cap) out[p] = ((uint32_t)rv << kIdBits) | (uint32_t)v;
                     else atomicOr(a.err, kErrList);
                 }
+                if (nl.ltop_out) nl.ltop_out[v] = (uint8_t)s_top;
                 record_change(a, nl, v, Skap, kappa);
                 atomicAdd(a.bytes, level1_bytes(e - b, Skap, 0));
             }
@@ -521,10 +532,12 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             const bool flat = mode == 0 && deg <= kFlatMax;
             if (flat) {
                 int cnt = 0;
+                const int t0 = s_t;
                 if (tid < deg) {
                     const int32_t w = a.col[b + tid];
                     int sz = 0;
-                    if (a.alive[w] == 1) sz = min(nl.lsz_in[w], (int)a.cap);
+                    // a list whose highest rank is below t has nothing to give
+                    if (a.alive[w] == 1 && (int)nl.ltop_in[w] >= t0) sz = min(nl.lsz_in[w], (int)a.cap);
                     s_w[tid] = w;
                     s_sz[tid] = sz;
                     s_dead[tid] = INT_MAX;
@@ -614,7 +627,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                         if (sz > pos) break;
                     } else {
                         const int32_t w = a.col[b + li];
-                        if (a.alive[w] == 1) {
+                        if (a.alive[w] == 1 && (int)nl.ltop_in[w] >= t) {
                             sz = min(nl.lsz_in[w], (int)a.cap);
                             lp = nl.keys_in + (size_t)w * (size_t)a.cap;
                             if (sz > pos) break;
@@ -756,6 +769,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 if (tid < 32) {
                     int above = 0;
                     for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
+                    __syncwarp();  // every lane has read before any lane writes
                     s_hist[tid] = above;
                 }
                 __syncthreads();
@@ -833,8 +847,12 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
                 // write members grouped by rank, highest first, emptying the table
                 if (tid < 32) {
+                    const uint32_t nz = __ballot_sync(kFull, tid >= kappa && s_hist[tid] > 0);
+                    if (tid == 0 && nl.ltop_out) nl.ltop_out[v] = (uint8_t)(nz ? 31 - __clz(nz) : 0);
+                    __syncwarp();
                     int above = 0;
                     for (int j = tid + 1; j < 32; ++j) above += s_hist[j];
+                    __syncwarp();
                     s_hist[tid] = above;  // start offset of rank tid
                 }
                 __syncthreads();
@@ -1135,6 +1153,7 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.keys = g.keys;
     a.lsz = g.lsz;
     a.lk = g.lk;
+    a.ltop = g.ltop;
     a.est = g.d64;
     a.worklist = worklist;
     a.d_count = d_count;
