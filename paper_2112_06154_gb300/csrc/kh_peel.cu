@@ -160,10 +160,16 @@ __global__ void k_min_lb(const uint8_t* __restrict__ alive, const uint8_t* __res
 }
 
 // Stale nodes with lb <= T = max(c, U) join the refine list and become fresh
-// (their value is recomputed right after, before anything reads it).
+// (their value is recomputed right after, before anything reads it).  A stale
+// node whose upper bound is already <= c leaves in this round whatever its
+// exact value (c' = max(c, min) >= c >= d), so it is not refined; its upper
+// bound joins the round minimum (mr), which keeps that minimum <= c and so
+// c' = c, as the exact values would (the true minimum is <= its bound <= c).
+// The replay of a given order (dense) needs every value and skips nothing.
+template <typename T>
 __global__ void k_collect(const uint8_t* __restrict__ alive, uint8_t* __restrict__ fresh, int64_t n,
-                          const int32_t* __restrict__ vl, LbArgs a, DevState* st, PeelState p,
-                          int32_t* __restrict__ out) {
+                          const int32_t* __restrict__ vl, LbArgs a, const T* __restrict__ d,
+                          int keep_all, DevState* st, PeelState p, int32_t* __restrict__ out) {
     if (st->n_alive == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -173,8 +179,13 @@ __global__ void k_collect(const uint8_t* __restrict__ alive, uint8_t* __restrict
         const int64_t v = i < n ? (vl ? vl[i] : i) : 0;
         if (i < n && alive[v] == 1 && !fresh[v]) {
             const int g = graph_of(p, v);
-            const unsigned long long T = p.c[g] > p.mu[g] ? p.c[g] : p.mu[g];
-            due = lower_bound(a, (int)v) <= T;
+            const unsigned long long ub = (unsigned long long)d[v];
+            if (!keep_all && ub <= p.c[g]) {
+                atomicMin(p.mr + g, ub);  // removed this round: no refine needed
+            } else {
+                const unsigned long long T = p.c[g] > p.mu[g] ? p.c[g] : p.mu[g];
+                due = lower_bound(a, (int)v) <= T;
+            }
         }
         const uint32_t m = __ballot_sync(kFull, due);
         int base = 0;
@@ -632,8 +643,14 @@ int refine(Graph& g, bool sampled, cudaStream_t s) {
     const int grid = peel_grid(g);
     const LbArgs la = lb_args(g);
     prof_begin(g, kProfPeel, s);
-    k_collect<<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.vcount, g.vlist, la, g.state,
-                                            peel_state(g), g.listB);
+    if (sampled)
+        k_collect<unsigned long long><<<grid, kPeelThreads, 0, s>>>(
+            g.alive, g.fresh, g.vcount, g.vlist, la, g.d64, g.dense ? 1 : 0, g.state, peel_state(g),
+            g.listB);
+    else
+        k_collect<int32_t><<<grid, kPeelThreads, 0, s>>>(g.alive, g.fresh, g.vcount, g.vlist, la,
+                                                         g.d32, g.dense ? 1 : 0, g.state,
+                                                         peel_state(g), g.listB);
     count_launch(g, 1);
     prof_end(g, kProfPeel, s);
     if (sampled) return launch_level(g, g.h, g.listB, &g.state->nQ, 0, 0, s, 2);
