@@ -388,13 +388,63 @@ __global__ void __launch_bounds__(kBfsThreads) k_hdeg(BfsArgs a) {
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
 }
 
+constexpr int kWarpRowX = 2048;   // longer rows are done by the whole block
+constexpr int kBlockHeavyX = 64;
+
+// One entry of a ball hop (all lanes of the warp together): u = col[k], when
+// k < e, is stamped at its first visit of the round, joins the next frontier if
+// a further hop below its h follows and, when alive, the stale list; hop 1 also
+// lowers the alive degree of R's alive neighbours.
+__device__ __forceinline__ void ball_entry(const int32_t* __restrict__ col,
+                                           const uint8_t* __restrict__ alive,
+                                           int32_t* __restrict__ seen, int32_t* __restrict__ fout,
+                                           int* nfout, int32_t* __restrict__ wl, int* nwl,
+                                           int h_all, int64_t cap, int32_t* __restrict__ degX,
+                                           const uint8_t* __restrict__ hv, int hop, int stamp,
+                                           int64_t k, int64_t e, int lane) {
+    bool isnew = false;
+    int32_t u = 0;
+    uint8_t au = 0;
+    int hu = h_all;
+    if (k < e) {
+        u = col[k];
+        au = alive[u];
+        if (hv) hu = (int)hv[u];  // batches: the h of u's graph
+        // hop 1 scans each removed node's row once: alive neighbours lose a degree
+        if (degX && au == 1) atomicSub(degX + u, 1);
+        if (au != 0 && hop < hu && *(volatile int32_t*)(seen + u) != stamp)
+            isnew = atomicExch(seen + u, stamp) != stamp;
+    }
+    const bool to_f = isnew && hop + 1 < hu;
+    const bool to_w = isnew && au == 1;
+    const uint32_t m1 = __ballot_sync(kFull, to_f);
+    const uint32_t m2 = __ballot_sync(kFull, to_w);
+    if (!(m1 | m2)) return;
+    int b1 = 0, b2 = 0;
+    if (lane == 0) {
+        if (m1) b1 = atomicAdd(nfout, __popc(m1));
+        if (m2) b2 = atomicAdd(nwl, __popc(m2));
+    }
+    b1 = __shfl_sync(kFull, b1, 0);
+    b2 = __shfl_sync(kFull, b2, 0);
+    const uint32_t lower = (1u << lane) - 1u;
+    if (to_f) {
+        const int p = b1 + __popc(m1 & lower);
+        if (p < cap) fout[p] = u;
+    }
+    if (to_w) {
+        const int p = b2 + __popc(m2 & lower);
+        if (p < cap) wl[p] = u;
+    }
+}
+
 // One hop of the ball around the removed set R in the OLD graph (alive != 0),
 // for hops 1 .. h-1: every newly reached vertex is stamped, joins the next
 // frontier (if a further hop below h follows) and, when it is still alive
 // (alive == 1), the stale list.  Hop 1 also lowers the alive degrees of R's
 // neighbours (with h = 1 it stamps nothing).  Nodes exactly h hops from R are
-// handled by the loss BFS instead.  One CTA per frontier vertex, so a hub's row
-// is spread over all of the CTA's warps.
+// handled by the loss BFS instead.  One warp per frontier vertex; rows longer
+// than kWarpRowX are gathered per block and spread over all its warps.
 __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                            const int32_t* __restrict__ fin, const int* __restrict__ nfin,
@@ -403,58 +453,50 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
                            unsigned long long* bytes, int32_t* __restrict__ degX,
                            const uint8_t* __restrict__ hv, int hop) {
     if (st->early) return;
+    __shared__ int s_heavy[kBlockHeavyX];
+    __shared__ int s_nheavy;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nin = *nfin;
     const int stamp = st->round * kPhaseStride;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_bytes = 0;
-    for (int64_t i = blockIdx.x; i < nin; i += gridDim.x) {
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
         const int w = fin[i];
         const int64_t b = rowptr[w], e = rowptr[w + 1];
-        if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
-        for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
-            const int64_t k = k0 + lane;
-            bool isnew = false;
-            int32_t u = 0;
-            uint8_t au = 0;
-            int hu = h_all;
-            if (k < e) {
-                u = col[k];
-                au = alive[u];
-                if (hv) hu = (int)hv[u];  // batches: the h of u's graph
-                // hop 1 scans each removed node's row once: alive neighbours lose a degree
-                if (degX && au == 1) atomicSub(degX + u, 1);
-                if (au != 0 && hop < hu && *(volatile int32_t*)(seen + u) != stamp)
-                    isnew = atomicExch(seen + u, stamp) != stamp;
-            }
-            const bool to_f = isnew && hop + 1 < hu;
-            const bool to_w = isnew && au == 1;
-            uint32_t m1 = __ballot_sync(kFull, to_f);
-            uint32_t m2 = __ballot_sync(kFull, to_w);
-            int b1 = 0, b2 = 0;
-            if (lane == 0) {
-                if (m1) b1 = atomicAdd(nfout, __popc(m1));
-                if (m2) b2 = atomicAdd(nwl, __popc(m2));
-            }
-            b1 = __shfl_sync(kFull, b1, 0);
-            b2 = __shfl_sync(kFull, b2, 0);
-            const uint32_t lower = (1u << lane) - 1u;
-            if (to_f) {
-                const int p = b1 + __popc(m1 & lower);
-                if (p < cap) fout[p] = u;
-            }
-            if (to_w) {
-                const int p = b2 + __popc(m2 & lower);
-                if (p < cap) wl[p] = u;
+        if (e - b > kWarpRowX) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
+            slot = __shfl_sync(kFull, slot, 0);
+            if (slot < kBlockHeavyX) {
+                if (lane == 0) s_heavy[slot] = w;
+                continue;
             }
         }
+        if (lane == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
+        for (int64_t k0 = b; k0 < e; k0 += 32)
+            ball_entry(col, alive, seen, fout, nfout, wl, nwl, h_all, cap, degX, hv, hop, stamp,
+                       k0 + lane, e, lane);
     }
-    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    __syncthreads();
+    const int nh = min(s_nheavy, kBlockHeavyX);
+    for (int j = 0; j < nh; ++j) {
+        const int w = s_heavy[j];
+        const int64_t b = rowptr[w], e = rowptr[w + 1];
+        if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
+        for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x)
+            ball_entry(col, alive, seen, fout, nfout, wl, nwl, h_all, cap, degX, hv, hop, stamp,
+                       k0 + lane, e, lane);
+    }
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 // Mark nodes stale and give each the lower bound max(deg_X(v), max_w deg_X(w))
 // of deg_h(v; X), h >= 2: N(v; h) contains N(w; 1) for every alive neighbour w.
 // The bound only depends on the 2-ball of v, which the h-ball refresh covers.
-// One CTA per node (hub rows are spread over the CTA).
+// One warp per node; rows longer than kWarpRowX go to the whole block.
 __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                               const uint8_t* __restrict__ alive, const int32_t* __restrict__ degX,
                               const int32_t* __restrict__ list, const int* __restrict__ nlist,
@@ -463,34 +505,66 @@ __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t*
                               unsigned long long* bytes, int h_all, const uint8_t* __restrict__ hv) {
     if (st->early) return;
     __shared__ int s_max[kBfsThreads / 32];
+    __shared__ int s_heavy[kBlockHeavyX];
+    __shared__ int s_nheavy;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t cnt = list ? (int64_t)(*nlist) : n;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_bytes = 0;
-    for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
         const int v = list ? list[i] : (int)i;
-        if (alive[v] != 1) continue;  // block-uniform
+        if (alive[v] != 1) continue;  // warp-uniform
         const int h = hv ? (int)hv[v] : h_all;
         const int64_t b = rowptr[v], e = rowptr[v + 1];
+        if (h >= 2 && e - b > kWarpRowX) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
+            slot = __shfl_sync(kFull, slot, 0);
+            if (slot < kBlockHeavyX) {
+                if (lane == 0) s_heavy[slot] = v;
+                continue;
+            }
+        }
         int m = 0;
         if (h >= 2) {
-            for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+            for (int64_t k = b + lane; k < e; k += 32) {
                 const int32_t w = col[k];
                 if (alive[w] == 1) m = max(m, degX[w]);
             }
+            for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_down_sync(kFull, m, off));
+        }
+        if (lane == 0) {
+            // h = 1: deg_1 = deg_X(v) itself; the neighbour term needs h >= 2
+            lb[v] = (unsigned long long)max(m, degX[v]);
+            fresh[v] = 0;
+            my_bytes += 8ull + 5ull * (unsigned long long)(e - b) + 13ull;
+        }
+    }
+    __syncthreads();
+    const int nh = min(s_nheavy, kBlockHeavyX);
+    for (int j = 0; j < nh; ++j) {
+        const int v = s_heavy[j];
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        int m = 0;
+        for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+            const int32_t w = col[k];
+            if (alive[w] == 1) m = max(m, degX[w]);
         }
         for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_down_sync(kFull, m, off));
         if (lane == 0) s_max[warp] = m;
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
-            // h = 1: deg_1 = deg_X(v) itself; the neighbour term needs h >= 2
             lb[v] = (unsigned long long)max(m, degX[v]);
             fresh[v] = 0;
             my_bytes += 8ull + 5ull * (unsigned long long)(e - b) + 13ull;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 // The nodes the loss BFS reached keep their state: d (exact when fresh, an

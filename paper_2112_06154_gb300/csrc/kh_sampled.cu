@@ -379,9 +379,14 @@ __device__ __forceinline__ int set_insert(uint32_t* tab, int lg, uint32_t key, i
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t s = ((key & kIdMask) * 0x9E3779B1u) >> (32 - lg);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const uint32_t prev = atomicCAS(tab + s, kEmpty, key);
-        if (prev == kEmpty) return (int)s;
-        if (prev == key) return -1;
+        // most keys of a union are repeats: a plain read settles them without an atomic
+        const uint32_t cur = *(volatile uint32_t*)(tab + s);
+        if (cur == key) return -1;
+        if (cur == kEmpty) {
+            const uint32_t prev = atomicCAS(tab + s, kEmpty, key);
+            if (prev == kEmpty) return (int)s;
+            if (prev == key) return -1;
+        }
         s = (s + 1u) & mask;
     }
     atomicOr(err, kErrProbe);
@@ -934,44 +939,91 @@ __device__ __forceinline__ bool level_may_change(const MarkFilter& f, int u, int
 // Alive neighbours of the listed nodes (two lists, the second optional and
 // rank-filtered) join the work list once per stamp (round, phase).  One CTA
 // per listed node.
+// (The CTA-wide path of the row kernels below: rows longer than kWarpRow are
+// gathered per block and done by all its warps after the warp-per-node pass.)
+constexpr int kWarpRow = 2048;
+constexpr int kBlockHeavy = 64;
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// Visit entries [k0 + lane, ...) of a listed node's row: mark each alive
+// neighbour that passes the filter once per stamp and append it to wl.
+__device__ __forceinline__ void mark_entry(const int32_t* __restrict__ col,
+                                           const uint8_t* __restrict__ alive,
+                                           int32_t* __restrict__ seen, int32_t* __restrict__ wl,
+                                           int* nwl, int64_t cap, const MarkFilter& f, bool filt,
+                                           int rw, int phase, int stamp, int64_t k, int64_t e,
+                                           int lane) {
+    bool isnew = false;
+    int32_t u = 0;
+    if (k < e) {
+        u = col[k];
+        if (alive[u] == 1 && (!filt || level_may_change(f, u, rw, phase)) &&
+            *(volatile int32_t*)(seen + u) != stamp)
+            isnew = atomicExch(seen + u, stamp) != stamp;
+    }
+    const uint32_t m = __ballot_sync(kFull, isnew);
+    if (!m) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(nwl, __popc(m));
+    base = __shfl_sync(kFull, base, 0);
+    if (isnew) {
+        const int p = base + __popc(m & ((1u << lane) - 1u));
+        if (p < cap) wl[p] = u;
+    }
+}
+
 __global__ void k_mark_nbrs(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                             const uint8_t* __restrict__ alive, int32_t* __restrict__ seen,
                             const int32_t* __restrict__ list1, const int* __restrict__ nlist1,
                             const int32_t* __restrict__ list2, const int* __restrict__ nlist2,
                             int32_t* __restrict__ wl, int* nwl, const DevState* __restrict__ st,
                             int phase, int64_t cap, unsigned long long* bytes, MarkFilter f) {
+    __shared__ int s_heavy[kBlockHeavy];
+    __shared__ int s_nheavy;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n1 = *nlist1;
     const int nin = n1 + (list2 ? *nlist2 : 0);
     const int stamp = st->round * kPhaseStride + phase;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_bytes = 0;
-    for (int64_t i = blockIdx.x; i < nin; i += gridDim.x) {
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    // one warp per listed node; rows longer than kWarpRow go to the block afterwards
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nin; i += nw) {
+        const int w = i < n1 ? list1[i] : list2[i - n1];
+        const int64_t b = rowptr[w], e = rowptr[w + 1];
+        if (e - b > kWarpRow) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
+            slot = __shfl_sync(kFull, slot, 0);
+            if (slot < kBlockHeavy) {
+                if (lane == 0) s_heavy[slot] = (int)i;
+                continue;
+            }
+        }
+        const bool filt = f.rho != nullptr && i >= n1;
+        const int rw = filt ? (int)f.rho[w] : 0;
+        if (lane == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
+        for (int64_t k0 = b; k0 < e; k0 += 32)
+            mark_entry(col, alive, seen, wl, nwl, cap, f, filt, rw, phase, stamp, k0 + lane, e, lane);
+    }
+    __syncthreads();
+    const int nh = min(s_nheavy, kBlockHeavy);
+    for (int j = 0; j < nh; ++j) {
+        const int i = s_heavy[j];
         const int w = i < n1 ? list1[i] : list2[i - n1];
         const bool filt = f.rho != nullptr && i >= n1;
         const int rw = filt ? (int)f.rho[w] : 0;
         const int64_t b = rowptr[w], e = rowptr[w + 1];
         if (threadIdx.x == 0) my_bytes += 12ull + 4ull * (unsigned long long)(e - b);
-        for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x) {
-            const int64_t k = k0 + lane;
-            bool isnew = false;
-            int32_t u = 0;
-            if (k < e) {
-                u = col[k];
-                if (alive[u] == 1 && (!filt || level_may_change(f, u, rw, phase)) &&
-                    *(volatile int32_t*)(seen + u) != stamp)
-                    isnew = atomicExch(seen + u, stamp) != stamp;
-            }
-            const uint32_t m = __ballot_sync(kFull, isnew);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(nwl, __popc(m));
-            base = __shfl_sync(kFull, base, 0);
-            if (isnew) {
-                const int p = base + __popc(m & ((1u << lane) - 1u));
-                if (p < cap) wl[p] = u;
-            }
-        }
+        for (int64_t k0 = b + warp * 32; k0 < e; k0 += blockDim.x)
+            mark_entry(col, alive, seen, wl, nwl, cap, f, filt, rw, phase, stamp, k0 + lane, e, lane);
     }
-    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 // Alg. 1 on a level list of size S and level kappa, with the node of rank
@@ -1002,14 +1054,54 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
                                 int64_t n, uint8_t* __restrict__ fresh,
                                 unsigned long long* __restrict__ lb, unsigned long long* bytes) {
     __shared__ unsigned long long s_max[kLuThreads / 32];
+    __shared__ int s_heavy[kBlockHeavy];
+    __shared__ int s_nheavy;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t cnt = list ? (int64_t)(*nlist) : n;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long my_bytes = 0;
-    for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    // one warp per node; rows longer than kWarpRow go to the block afterwards
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
         const int v = list ? list[i] : (int)i;
-        if (alive[v] != 1) continue;  // block-uniform
+        if (alive[v] != 1) continue;  // warp-uniform
         const int h = hv ? (int)hv[v] : h_all;
         if (only_h && h != only_h) continue;
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        if (e - b > kWarpRow) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
+            slot = __shfl_sync(kFull, slot, 0);
+            if (slot < kBlockHeavy) {
+                if (lane == 0) s_heavy[slot] = v;
+                continue;
+            }
+        }
+        const int64_t M = Mv ? (int64_t)Mv[v] : M_all;
+        const int32_t* lsz_prev = h >= 2 ? lsz + (size_t)(h - 2) * (size_t)n : nullptr;
+        const uint8_t* lk_prev = h >= 2 ? lk + (size_t)(h - 2) * (size_t)n : nullptr;
+        unsigned long long m = 0;
+        if (lsz_prev) {
+            const int rv = rank[v];
+            for (int64_t k = b + lane; k < e; k += 32) {
+                const int32_t w = col[k];
+                if (alive[w] == 1) m = umax64(m, est_first(lsz_prev[w], lk_prev[w], rv, M));
+            }
+            for (int off = 16; off > 0; off >>= 1) m = umax64(m, __shfl_down_sync(kFull, m, off));
+            m = umax64(m, est_first(lsz_prev[v], lk_prev[v], rv, M));
+        }
+        if (lane == 0) {
+            lb[v] = m;
+            fresh[v] = 0;
+            my_bytes += 29ull + 9ull * (unsigned long long)(e - b);
+        }
+    }
+    __syncthreads();
+    const int nh = min(s_nheavy, kBlockHeavy);
+    for (int j = 0; j < nh; ++j) {
+        const int v = s_heavy[j];
+        const int h = hv ? (int)hv[v] : h_all;
         const int64_t M = Mv ? (int64_t)Mv[v] : M_all;
         const int32_t* lsz_prev = h >= 2 ? lsz + (size_t)(h - 2) * (size_t)n : nullptr;
         const uint8_t* lk_prev = h >= 2 ? lk + (size_t)(h - 2) * (size_t)n : nullptr;
@@ -1019,22 +1111,14 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
             const int rv = rank[v];
             for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
                 const int32_t w = col[k];
-                if (alive[w] == 1) {
-                    const unsigned long long x = est_first(lsz_prev[w], lk_prev[w], rv, M);
-                    if (x > m) m = x;
-                }
+                if (alive[w] == 1) m = umax64(m, est_first(lsz_prev[w], lk_prev[w], rv, M));
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                const unsigned long long o = __shfl_down_sync(kFull, m, off);
-                if (o > m) m = o;
-            }
+            for (int off = 16; off > 0; off >>= 1) m = umax64(m, __shfl_down_sync(kFull, m, off));
             if (lane == 0) s_max[warp] = m;
             __syncthreads();
             if (threadIdx.x == 0) {
-                for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                    if (s_max[w] > m) m = s_max[w];
-                const unsigned long long own = est_first(lsz_prev[v], lk_prev[v], rv, M);
-                if (own > m) m = own;
+                for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = umax64(m, s_max[w]);
+                m = umax64(m, est_first(lsz_prev[v], lk_prev[v], rv, M));
             }
         }
         if (threadIdx.x == 0) {
@@ -1044,7 +1128,8 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
 }
 
 }  // namespace
