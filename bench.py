@@ -171,6 +171,11 @@ def parse():
                    help="--op only: R-MAT scale of the graph (a smaller case for profilers)")
     p.add_argument("--variant", default=None,
                    help="--op hdeg2/counts2 only: force the 2-degree layout, 'cta' or 'sliced,S,T'")
+    p.add_argument("--union", choices=["auto", "stepped", "free"], default="auto",
+                   help="schedule of the level-union kernel (kh_set_variant KH_OP_LEVEL_UNION)")
+    p.add_argument("--prof", action="store_true",
+                   help="--op only: bracket the kernel classes and print their times and "
+                        "algorithmic bytes")
     p.add_argument("--requests", type=int, default=300)
     p.add_argument("--rate", type=float, default=200.0)
     p.add_argument("--pool", type=int, default=24)
@@ -179,6 +184,11 @@ def parse():
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--exact-graphs", type=int, default=512)
     return p.parse_args()
+
+
+def apply_union(K, G, args):
+    mode = {"auto": K.KH_VAR_AUTO, "stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE}
+    K.kh_set_variant(G, mode[getattr(args, "union", "auto")], op=K.KH_OP_LEVEL_UNION)
 
 
 def dist_env():
@@ -299,6 +309,7 @@ def run_ours(args):
     ctx = K.kh_ctx_create(dev, stream)
     G = K.kh_graph_load_csr(ctx, rp, cl)
     K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+    apply_union(K, G, args)
     M = K.kh_get_M(G)
     out = wl.device_outputs(n)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -341,6 +352,7 @@ def run_ours(args):
         d2h = wl.d2h_bytes(n)
         Gw = K.kh_graph_load_csr(ctx, prp, pcl)  # warm-up
         K.kh_set_sampling(Gw, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+        apply_union(K, Gw, args)
         wl.step(K, Gw, n)
         Gw.close()
         barrier()
@@ -352,6 +364,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             Ge = K.kh_graph_load_csr(ctx, prp, pcl)
             K.kh_set_sampling(Ge, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+            apply_union(K, Ge, args)
             upd_e2e += wl.step(K, Ge, n)
             K.kh_sync(Ge)
             t_e2e += time.perf_counter() - t0
@@ -487,6 +500,7 @@ def run_op(args):
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rp, cl)
     K.kh_set_sampling(G, seed=RANK_SEED, M=0, eps=EPS, delta=DELTA)
+    apply_union(K, G, args)
     op, h = args.op[:-1], int(args.op[-1])
     K.kh_set_h(G, h)
     if args.variant:
@@ -495,6 +509,8 @@ def run_op(args):
             K.kh_set_variant(G, K.KH_VAR_CTA)
         else:
             K.kh_set_variant(G, K.KH_VAR_SLICED, int(f[1]), int(f[2]))
+    if args.prof:
+        K.kh_prof_enable(G, True)
     t0 = time.perf_counter()
     fn = {"hdeg": K.kh_hdegree_exact, "counts": lambda g: K.kh_sampled_counts(g, J_LO, J_HI),
           "est": K.kh_estimate, "sampled": K.kh_core_sampled, "exact": K.kh_core_exact}[op]
@@ -502,6 +518,14 @@ def run_op(args):
     K.kh_sync(G)
     secs = time.perf_counter() - t0
     info = {"op": args.op, "seconds": secs, "launches": K.kh_launch_count(G), "n": int(rp.size - 1)}
+    if args.prof:
+        info["classes"] = {}
+        for kind in range(K.KH_PROF_KINDS):
+            ms, nl, byts = K.kh_prof_read(G, kind)
+            if nl:
+                info["classes"][K.PROF_NAMES[kind]] = {
+                    "ms": ms, "launches": nl, "alg_bytes": byts,
+                    "per_launch_ms": K.kh_prof_trace(G, kind).tolist()[:8]}
     if op in ("hdeg", "counts") and h == 2:
         info["variant"] = K.kh_get_variant(G)
     print(json.dumps(info), flush=True)
@@ -524,7 +548,8 @@ def run_rmat_ops(args):
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rowptr, col)
     K.kh_set_sampling(G, seed=1)
-    out = {"workload": "rmat_scale22_ops", "impl": "ours", "graph": stats, "M": K.kh_get_M(G),
+    apply_union(K, G, args)
+    out = {"workload": "rmat_scale22_ops", "impl": "ours", "union": args.union, "graph": stats, "M": K.kh_get_M(G),
            "gen_s": gen_s, "unit": "s", "higher_is_better": False}
 
     def timed(fn):

@@ -275,6 +275,15 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
 #define KH_OP_PEEL_COMPACT 1
 #define KH_COMPACT_OFF 1
 #define KH_COMPACT_ALWAYS 2
+/* KH_OP_LEVEL_UNION: how the level >= 2 list union (Alg. 2 with Alg. 5's
+ * trim) schedules a node's lists over the warps of its CTA.
+ * KH_LEVELU_STEPPED: barrier-separated steps, the trim once per step;
+ * KH_LEVELU_FREE: warps claim lists and trim from their own view of the rank
+ * counts, meeting only to compact the hash set.  KH_VAR_AUTO: stepped.  The
+ * lists are the same either way. */
+#define KH_OP_LEVEL_UNION 2
+#define KH_LEVELU_STEPPED 1
+#define KH_LEVELU_FREE 2
 int kh_set_variant(kh_graph *g, int32_t op, int32_t variant, int32_t slices, int32_t threads);
 int kh_get_variant(kh_graph *g, int32_t op, int32_t *variant, int32_t *slices, int32_t *threads,
                    double *tuned_ms);

@@ -420,6 +420,178 @@ size_t levelU_smem(int lg) {
     return hcap * 4 + (hcap >> 1) * 4 + hcap * 2;
 }
 
+// Drop the keys below t from the hash set: empty their slots, re-insert the
+// rest (all threads of the CTA).
+__device__ __forceinline__ void compact_set(uint32_t* tab, uint32_t* stage, uint16_t* used, int lg,
+                                            int hcap, int tc, int* s_nused, int* s_nstage,
+                                            int* err) {
+    const int tid = threadIdx.x;
+    const int nu = min(*s_nused, hcap);
+    if (tid == 0) *s_nstage = 0;
+    __syncthreads();
+    for (int i = tid; i < nu; i += blockDim.x) {
+        const int slot = used[i];
+        const uint32_t key = tab[slot];
+        tab[slot] = kEmpty;
+        if ((int)(key >> kIdBits) >= tc) {
+            const int p = atomicAdd(s_nstage, 1);
+            if (p < (hcap >> 1)) stage[p] = key;
+            else atomicOr(err, kErrProbe);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *s_nused = 0;
+    __syncthreads();
+    const int ns = min(*s_nstage, hcap >> 1);
+    for (int i = tid; i < ns; i += blockDim.x) {
+        const int slot = set_insert(tab, lg, stage[i], err);
+        if (slot >= 0) used[atomicAdd(s_nused, 1)] = (uint16_t)slot;
+    }
+    __syncthreads();
+}
+
+// The warp's view of the union's rank counts: lane j gets S_j = #{distinct
+// keys inserted so far with rank >= j}.  Read while other warps insert, the
+// counts are those of a subset of the union (each rank class read at one
+// moment), so every level derived from them is at most the final one and the
+// partial estimate is at most the final estimate (Prop. 4.2).
+__device__ __forceinline__ int snapshot_counts(const int* s_hist, int lane) {
+    int S = *(volatile const int*)(s_hist + lane);
+    for (int off = 1; off < 32; off <<= 1) {
+        const int x = __shfl_down_sync(kFull, S, off);
+        if (lane + off < 32) S += x;
+    }
+    return S;
+}
+
+// The union of free-running warps (k_levelU<true>): each warp claims whole
+// lists from a shared counter and reads each in 128-key chunks (four keys per
+// lane) until a key below the running level t shows (lists are grouped by
+// rank, highest first).  After every chunk the warp raises t from its
+// snapshot of the rank counts (Alg. 5's trim) and, in a refine, tests the
+// partial estimate against T.  The CTA meets at a barrier only to compact the
+// set (once it holds more than half its slots: at most one chunk per warp
+// and one more from each other warp follow before they stop, so the set
+// never fills) and at the end, where warp 0 trims from the complete counts.
+// Returns true when the refine stopped early (s_part holds the bound).
+__device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& nl, uint32_t* tab,
+                                        uint32_t* stage, uint16_t* used, int lg, int hcap,
+                                        int* s_hist, int* s_t, int* s_nused, int* s_nstage,
+                                        int* s_exit, unsigned long long* s_part, int* s_item,
+                                        int* s_creq, unsigned long long T, int vin, bool can_stop,
+                                        int mode, int first, int64_t b, int l0, int L, int rv,
+                                        unsigned long long& my_bytes) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        *s_item = 0;
+        *s_creq = 0;
+    }
+    __syncthreads();
+    int cli = -1, cpos = 0, csz = 0;  // this warp's open list (kept across a compaction)
+    const uint32_t* clp = nullptr;
+    for (;;) {
+        for (;;) {
+            if (*(volatile int*)s_creq || *(volatile int*)s_exit) break;
+            if (cli < 0) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(s_item, 1);
+                c = __shfl_sync(kFull, c, 0);
+                if (c >= L) break;
+                cli = l0 + c;
+                cpos = 0;
+                csz = 0;
+                if (mode == 2) {
+                    csz = __ldcg(a.part_size + first + cli);
+                    clp = a.part_keys + (size_t)(first + cli) * (size_t)a.cap;
+                } else {
+                    const int32_t w = a.col[b + cli];
+                    // a list whose highest rank is below t has nothing to give
+                    if (a.alive[w] == 1 && (int)nl.ltop_in[w] >= *(volatile int*)s_t) {
+                        csz = min(nl.lsz_in[w], (int)a.cap);
+                        clp = nl.keys_in + (size_t)w * (size_t)a.cap;
+                    }
+                }
+                if (cpos >= csz) {
+                    cli = -1;
+                    continue;
+                }
+            }
+            const int t = *(volatile int*)s_t;
+            const int p = cpos + lane * kKeysPerLane;
+            bool below = false;
+            if (p < csz) {
+                const uint4 k4 = mode == 2 ? __ldcg(reinterpret_cast<const uint4*>(clp + p))
+                                           : *reinterpret_cast<const uint4*>(clp + p);
+                const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+                for (int q = 0; q < kKeysPerLane; ++q) {
+                    if (p + q < csz) {
+                        const uint32_t key = kk[q];
+                        const int r = (int)(key >> kIdBits);
+                        if (mode != 2) my_bytes += 4;
+                        if (r >= t) {
+                            const int slot = set_insert(tab, lg, key, a.err);
+                            if (slot >= 0) {
+                                const int u = atomicAdd(s_nused, 1);
+                                if (u < hcap) used[u] = (uint16_t)slot;
+                                else atomicOr(a.err, kErrProbe);
+                                atomicAdd(&s_hist[r], 1);
+                            }
+                        } else {
+                            below = true;
+                        }
+                    }
+                }
+            }
+            cpos += kChunkKeys;
+            // ranks only fall along a list: after a key below t the rest is below t
+            if (__any_sync(kFull, below) || cpos >= csz) cli = -1;
+            // trim from this warp's snapshot; the early-stop test in a refine
+            const int S = snapshot_counts(s_hist, lane);
+            const uint32_t over = __ballot_sync(kFull, S > nl.M);
+            const int pmax = over ? 31 - __clz(over) : -1;
+            if (lane == 0 && pmax + 1 > t) atomicMax(s_t, pmax + 1);
+            if (can_stop) {
+                const int Sp = S + ((!vin && rv >= lane) ? 1 : 0);
+                const uint32_t fits = __ballot_sync(kFull, Sp <= nl.M);
+                const int k = fits ? __ffs(fits) - 1 : 32;
+                const int Sk = __shfl_sync(kFull, Sp, k & 31);
+                const unsigned long long pe = estimate_of(k < 32 ? Sk : 0, k, rv, nl.M);
+                if (lane == 0 && pe > T) {
+                    atomicMax(s_part, pe);
+                    atomicCAS(s_exit, 0, 1);
+                }
+                // a part stops too once another part of the node has shown d(v) > T
+                if (mode == 1 && lane == 0 && ld_acquire(a.part_stop + first)) atomicCAS(s_exit, 0, 2);
+            }
+            if (lane == 0 && *(volatile int*)s_nused > (hcap >> 1)) *(volatile int*)s_creq = 1;
+        }
+        __syncthreads();
+        if (*(volatile int*)s_exit) return true;
+        if (!*(volatile int*)s_creq) break;  // every list claimed and read
+        // compaction: trim from the complete counts first, then drop keys below t
+        if (tid < 32) {
+            const int S = snapshot_counts(s_hist, lane);
+            const uint32_t over = __ballot_sync(kFull, S > nl.M);
+            const int pmax = over ? 31 - __clz(over) : -1;
+            if (lane == 0 && pmax + 1 > *s_t) *s_t = pmax + 1;
+        }
+        __syncthreads();
+        compact_set(tab, stage, used, lg, hcap, *s_t, s_nused, s_nstage, a.err);
+        if (tid == 0) *s_creq = 0;
+        __syncthreads();
+    }
+    // the level from the complete counts
+    if (tid < 32) {
+        const int S = snapshot_counts(s_hist, lane);
+        const uint32_t over = __ballot_sync(kFull, S > nl.M);
+        const int pmax = over ? 31 - __clz(over) : -1;
+        if (lane == 0 && pmax + 1 > *s_t) *s_t = pmax + 1;
+    }
+    __syncthreads();
+    return false;
+}
+
 // Heavy nodes (degree > kSplitDeg) are split: part j unions the lists of
 // neighbours [j kSplitChunk, (j+1) kSplitChunk) into its own trimmed partial
 // set, and the CTA that finishes a node's last part merges the partial sets.
@@ -429,6 +601,9 @@ size_t levelU_smem(int lg) {
 // some partial set, and for j >= t* = max_p t_p the counts S_j of the union of
 // the partial sets equal those of the full union.  The merge therefore runs the
 // same running-threshold union over the partial sets from t = t*.
+// FREE: the union's warps run free instead of in barrier-separated steps (see
+// the FREE branch below); both give the same lists.
+template <bool FREE>
 __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int hcap = 1 << lg;
@@ -439,6 +614,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
     __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
     __shared__ int s_vin, s_exit;                // own key in the table; early stop taken
     __shared__ int s_rho, s_last;
+    __shared__ int s_item, s_creq;              // free mode: list claims; compaction request
     __shared__ unsigned long long s_T, s_part;  // early-stop threshold; partial estimate
     // flat mode (degree <= kFlatMax): per neighbour list its node, size, first
     // chunk index (exclusive prefix of 128-key chunk counts) and the first
@@ -498,6 +674,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 s_nused = 0;
                 s_vin = 0;
                 s_exit = 0;
+                s_part = 0;
                 unsigned long long T = ~0ull;
                 if (a.stop_c && nl.last && mode != 2) {
                     const int g = a.gid ? a.gid[v] : 0;
@@ -530,6 +707,12 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                 }
             }
             __syncthreads();
+            bool stopped = false;
+            if constexpr (FREE) {
+                stopped = free_union(a, nl, tab, stage, used, lg, hcap, s_hist, &s_t, &s_nused,
+                                     &s_nstage, &s_exit, &s_part, &s_item, &s_creq, s_T, s_vin,
+                                     can_stop, mode, first, b, l0, L, rv, my_bytes);
+            } else {
             // Flat mode, whole nodes of degree <= kFlatMax: every (list, 128-key
             // chunk) pair is one work item, warps take items in order, one per
             // step, so long and short lists balance; a list is dropped once a
@@ -573,7 +756,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
             const int step = kKeysPerLane * G;
             int li = l0 + gid;  // list index of this group's current list
             int pos = 0;
-            bool any = true, stopped = false;
+            bool any = true;
             while (any) {
                 const int t = *(volatile int*)&s_t;
                 if (flat) {
@@ -742,6 +925,7 @@ __global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
                     __syncthreads();
                 }
             }
+            }  // stepped union
             if (stopped) {
                 // d(v) > T: v stays stale, its lower bound raised to the partial estimate
                 const int nu = min(s_nused, hcap);
@@ -1315,10 +1499,11 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
     const size_t dyn = levelU_smem(lg);
-    e = cudaFuncSetAttribute(k_levelU, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    void (*kern)(LevelArgs, int) = g.levelu_mode == KH_LEVELU_FREE ? k_levelU<true> : k_levelU<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levelU, kLuThreads, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLuThreads, dyn);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "occupancy(k_levelU)");
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)g.ctx->sm_count * per_sm;
@@ -1342,7 +1527,7 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     } else {
         a.n_sub = nullptr;
     }
-    k_levelU<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
+    kern<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
     count_launch(g, 1);
     prof_end(g, kProfLevelU, s);
     return KH_OK;

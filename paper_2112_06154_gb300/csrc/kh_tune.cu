@@ -247,6 +247,12 @@ extern "C" int kh_set_variant(kh_graph* G, int32_t op, int32_t variant, int32_t 
         g.compact_mode = variant;
         return KH_OK;
     }
+    if (op == KH_OP_LEVEL_UNION) {
+        if (variant != KH_VAR_AUTO && variant != KH_LEVELU_STEPPED && variant != KH_LEVELU_FREE)
+            return kh::set_error(g.ctx, KH_EINVAL, "unknown union schedule %d", variant);
+        g.levelu_mode = variant;
+        return KH_OK;
+    }
     if (op != KH_OP_HDEG2) return kh::set_error(g.ctx, KH_EINVAL, "unknown operation %d", op);
     if (variant == KH_VAR_AUTO) {
         g.force_hdeg2 = kh::TuneChoice{};
@@ -273,8 +279,8 @@ extern "C" int kh_get_variant(kh_graph* G, int32_t op, int32_t* variant, int32_t
                               int32_t* threads, double* tuned_ms) {
     if (!G) return KH_EINVAL;
     kh::Graph& g = G->g;
-    if (op == KH_OP_PEEL_COMPACT) {
-        if (variant) *variant = g.compact_mode;
+    if (op == KH_OP_PEEL_COMPACT || op == KH_OP_LEVEL_UNION) {
+        if (variant) *variant = op == KH_OP_PEEL_COMPACT ? g.compact_mode : g.levelu_mode;
         if (slices) *slices = 0;
         if (threads) *threads = 0;
         if (tuned_ms) *tuned_ms = 0.0;

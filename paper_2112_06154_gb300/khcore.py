@@ -36,6 +36,9 @@ KH_VAR_SLICED = 2
 KH_OP_PEEL_COMPACT = 1
 KH_COMPACT_OFF = 1
 KH_COMPACT_ALWAYS = 2
+KH_OP_LEVEL_UNION = 2
+KH_LEVELU_STEPPED = 1
+KH_LEVELU_FREE = 2
 PROF_NAMES = ["bfs", "level1", "levelU", "frontier", "peel"]
 
 _ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",
