@@ -99,6 +99,18 @@ int kh_graph_load_batch(kh_ctx *ctx, int32_t ngraphs, const int64_t *vtx_off, co
                         const int32_t *col, const int32_t *h_per_graph, uint32_t flags,
                         kh_graph **out);
 
+/* Before loading a graph (no counterpart in the paper; for callers that admit
+ * work by device memory): the budget M in force for n nodes (M_or_0 > 0, else
+ * Eq. (buffer) of eps and delta, as kh_set_sampling) into *M_out, and into
+ * *bytes an upper bound of the device memory the library allocates for a
+ * graph of n nodes and nnz adjacency entries and a sampled decomposition
+ * (kh_core_sampled) at this h: the CSR, the per-node work arrays, the level
+ * lists of levels 1..h-1, the split-part slots and the compaction buffers.
+ * Either output may be NULL.  Host only: no device is touched.  KH_EINVAL for
+ * negative sizes, h outside [1, 16], or M outside [1, 12000]. */
+int kh_footprint(int64_t n, int64_t nnz, int32_t h, int64_t M_or_0, double eps, double delta,
+                 int64_t *M_out, int64_t *bytes);
+
 /* Number of nodes of a loaded graph. */
 int kh_graph_n(kh_graph *g, int64_t *n);
 

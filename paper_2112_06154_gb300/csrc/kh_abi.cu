@@ -82,6 +82,7 @@ int ensure_work(Graph& g) {
         KH_CUDA_TRY(g.ctx, cudaMemset(g.loss, 0, sizeof(int32_t) * (n ? n : 1)));
     }
     if ((rc = dalloc(g.ctx, &g.listL, n, "listL"))) return rc;
+    if ((rc = ensure_bestnb(g, g.ctx->stream))) return rc;
     const size_t ng = (size_t)(g.gid ? g.ngraphs : 1);
     if ((rc = dalloc(g.ctx, &g.pc, ng, "per-graph c"))) return rc;
     if ((rc = dalloc(g.ctx, &g.pmn, ng, "per-graph minimum"))) return rc;
@@ -256,6 +257,7 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.degX);
     dfree(&g.lb64);
     dfree(&g.order2);
+    dfree(&g.bestnb);
     for (int b = 0; b < 2; ++b) {
         dfree(&g.cp_row[b]);
         dfree(&g.cp_col[b]);
@@ -546,6 +548,37 @@ int kh_graph_free(kh_graph* G) {
     cudaStreamSynchronize(G->g.ctx->stream);
     kh::free_graph_arrays(G->g);
     free(G);
+    return KH_OK;
+}
+
+int kh_footprint(int64_t n, int64_t nnz, int32_t h, int64_t M_or_0, double eps, double delta,
+                 int64_t* M_out, int64_t* bytes) {
+    if (n < 0 || nnz < 0 || h < 1 || h > kh::kMaxH || M_or_0 < 0) return KH_EINVAL;
+    int64_t M = M_or_0;
+    if (M == 0) {
+        if (!(eps > 0.0) || !(delta > 0.0) || !(delta < 1.0) || !std::isfinite(eps)) return KH_EINVAL;
+        M = kh::budget_M(n > 0 ? n : 1, eps, delta);
+    }
+    if (M < 1 || M > kh::kMaxM) return KH_EINVAL;
+    if (M_out) *M_out = M;
+    if (!bytes) return KH_OK;
+    const int64_t cap = (M + 3) & ~(int64_t)3;
+    // the graph: CSR, ranks, state
+    int64_t b = 8 * (n + 1) + 4 * nnz + n + (int64_t)sizeof(kh::DevState);
+    // per-node work arrays of ensure_work (alive, d, core, rounds, stamps, seven
+    // node lists, fresh, degrees, bounds, loss and its list, best neighbours,
+    // removed-node bitmap)
+    b += n * (1 + 4 + 8 + 4 + 8 + 4 + 4 + 7 * 4 + 1 + 4 + 8 + 4 + 4 + 4) + n / 8 + 64;
+    // level lists 1..h-1 (cap keys per node and level), sizes and levels of
+    // 1..h, change ranks, top ranks
+    b += (int64_t)(h - 1) * n * cap * 4 + (int64_t)h * n * 5 + n + (int64_t)(h - 1) * n;
+    // split parts of heavy nodes: at most nnz / 1365 slots (ceil(deg/2048) <=
+    // deg/1365 for deg > 4096), each cap keys plus counters
+    const int64_t parts = nnz / 1365;
+    b += parts * (cap * 4 + 29) + 4 * n;
+    // the peel's compaction buffers (graphs of at least 65536 nodes)
+    if (n >= 65536) b += 2 * 8 * (n + 1) + 2 * 4 * nnz + 2 * 4 * (n + 1) + 16 * (n + 1) + 64 * 1024;
+    *bytes = b + (1 << 20);
     return KH_OK;
 }
 

@@ -497,12 +497,17 @@ __global__ void k_ball_hop(const int64_t* __restrict__ rowptr, const int32_t* __
 // of deg_h(v; X), h >= 2: N(v; h) contains N(w; 1) for every alive neighbour w.
 // The bound only depends on the 2-ball of v, which the h-ball refresh covers.
 // One warp per node; rows longer than kWarpRowX go to the whole block.
+// (A row longer than kStaleScanX takes the neighbour term from its neighbour
+// of largest degree alone while that one is alive: still a lower bound.)
+constexpr int kStaleScanX = 64;
+
 __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                               const uint8_t* __restrict__ alive, const int32_t* __restrict__ degX,
                               const int32_t* __restrict__ list, const int* __restrict__ nlist,
                               int64_t n, uint8_t* __restrict__ fresh,
                               unsigned long long* __restrict__ lb, const DevState* __restrict__ st,
-                              unsigned long long* bytes, int h_all, const uint8_t* __restrict__ hv) {
+                              unsigned long long* bytes, int h_all, const uint8_t* __restrict__ hv,
+                              const int32_t* __restrict__ bestnb) {
     if (st->early) return;
     __shared__ int s_max[kBfsThreads / 32];
     __shared__ int s_heavy[kBlockHeavyX];
@@ -518,6 +523,14 @@ __global__ void k_stale_exact(const int64_t* __restrict__ rowptr, const int32_t*
         if (alive[v] != 1) continue;  // warp-uniform
         const int h = hv ? (int)hv[v] : h_all;
         const int64_t b = rowptr[v], e = rowptr[v + 1];
+        if (bestnb && h >= 2 && e - b > kStaleScanX && alive[bestnb[v]] == 1) {
+            if (lane == 0) {
+                lb[v] = (unsigned long long)max(degX[bestnb[v]], degX[v]);
+                fresh[v] = 0;
+                my_bytes += 8ull + 5ull + 13ull;
+            }
+            continue;
+        }
         if (h >= 2 && e - b > kWarpRowX) {
             int slot = 0;
             if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
@@ -592,6 +605,27 @@ __global__ void k_apply_loss(const int32_t* __restrict__ list, const int* __rest
     }
 }
 
+// The neighbour of largest degree of each node (ties: the smaller id; -1 for
+// an isolated node), one warp per node.
+__global__ void k_best_nb(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                          int64_t n, int32_t* __restrict__ best) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nw) {
+        long long key = -1;  // (degree << 32) | (0x7fffffff - id): max picks largest degree, smallest id
+        for (int64_t k = rowptr[v] + lane; k < rowptr[v + 1]; k += 32) {
+            const int32_t w = col[k];
+            const long long kk = ((long long)(rowptr[w + 1] - rowptr[w]) << 32) | (long long)(0x7fffffff - w);
+            key = key > kk ? key : kk;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const long long o = __shfl_down_sync(kFull, key, off);
+            key = key > o ? key : o;
+        }
+        if (lane == 0) best[v] = key < 0 ? -1 : (int32_t)(0x7fffffff - (int32_t)(key & 0x7fffffff));
+    }
+}
+
 int pick_grid(int sm, int per_sm, int64_t work) {
     int64_t g = (int64_t)sm * per_sm;
     if (work < g) g = work;
@@ -599,6 +633,16 @@ int pick_grid(int sm, int per_sm, int64_t work) {
 }
 
 }  // namespace
+
+int ensure_bestnb(Graph& g, cudaStream_t s) {
+    if (g.bestnb || g.n == 0) return KH_OK;
+    int rc = alloc_bytes(g.ctx, (void**)&g.bestnb, sizeof(int32_t) * (size_t)g.n, "best neighbours");
+    if (rc) return rc;
+    k_best_nb<<<pick_grid(g.ctx->sm_count, 8, (g.n * 32 + 255) / 256), 256, 0, s>>>(g.rowptr, g.col,
+                                                                                   g.n, g.bestnb);
+    count_launch(g, 1);
+    return KH_OK;
+}
 
 void launch_ranks(const Graph& g, cudaStream_t s) {
     if (g.n == 0) return;
@@ -724,7 +768,7 @@ void launch_stale_exact(Graph& g, const int* list, const int* d_count, cudaStrea
     prof_begin(g, kProfFrontier, s);
     k_stale_exact<<<grid, kBfsThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.degX, list, d_count, g.n,
                                        g.fresh, g.lb64, g.state, &g.state->bytes[kProfFrontier],
-                                       g.h, g.hv);
+                                       g.h, g.hv, g.bestnb);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

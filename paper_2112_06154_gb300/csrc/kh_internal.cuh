@@ -130,6 +130,8 @@ struct NvtxRange {
 
 // ---- launchers (kh_exact.cu) -------------------------------------------------
 void launch_ranks(const Graph& g, cudaStream_t s);
+// each node's neighbour of largest degree (computed once per graph, before a peel)
+int ensure_bestnb(Graph& g, cudaStream_t s);
 void launch_validate(const Graph& g, int* d_err, cudaStream_t s);
 // exact h-degrees of `count` nodes (worklist == nullptr: nodes 0..n-1) into deg32;
 // when cnt != nullptr also the fixed-level counts for j in [jlo, jlo+nj).
@@ -340,6 +342,8 @@ struct Graph {
     // sliced 2-degree kernel: sources longest first (non-isolated nodes only)
     int32_t *order2;
     int64_t nsrc2;
+    // each node's neighbour of largest degree (-1: none), for cheap stale bounds
+    int32_t *bestnb;
     // the 2-degree pass layout: forced by kh_set_variant, or chosen by the tuner
     TuneChoice force_hdeg2;
     TuneChoice tuned_hdeg2;

@@ -1229,6 +1229,12 @@ __device__ __forceinline__ unsigned long long est_first(int S, int kappa, int r_
 // levels are read.  One CTA per node.
 // Batches: a node's h and M come from its graph, and only nodes whose last
 // level is `only_h` (when nonzero) are marked.
+// A row longer than kStaleScan takes its neighbour term from the neighbour
+// of largest degree alone (bestnb) while that neighbour is alive: any alive
+// neighbour w gives a sub-multiset N(w; h-1) of N(v; h) led by v, so one
+// neighbour's term is still a lower bound, at O(1) cost instead of O(deg).
+constexpr int kStaleScan = 64;
+
 __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const uint8_t* __restrict__ alive, const uint8_t* __restrict__ rank,
                                 const int32_t* __restrict__ lsz, const uint8_t* __restrict__ lk,
@@ -1236,7 +1242,8 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
                                 const int32_t* __restrict__ Mv, int only_h,
                                 const int32_t* __restrict__ list, const int* __restrict__ nlist,
                                 int64_t n, uint8_t* __restrict__ fresh,
-                                unsigned long long* __restrict__ lb, unsigned long long* bytes) {
+                                unsigned long long* __restrict__ lb, unsigned long long* bytes,
+                                const int32_t* __restrict__ bestnb) {
     __shared__ unsigned long long s_max[kLuThreads / 32];
     __shared__ int s_heavy[kBlockHeavy];
     __shared__ int s_nheavy;
@@ -1253,6 +1260,21 @@ __global__ void k_stale_sampled(const int64_t* __restrict__ rowptr, const int32_
         const int h = hv ? (int)hv[v] : h_all;
         if (only_h && h != only_h) continue;
         const int64_t b = rowptr[v], e = rowptr[v + 1];
+        if (bestnb && h >= 2 && e - b > kStaleScan) {
+            const int w = bestnb[v];
+            if (alive[w] == 1) {  // warp-uniform
+                if (lane == 0) {
+                    const int64_t M = Mv ? (int64_t)Mv[v] : M_all;
+                    const size_t off = (size_t)(h - 2) * (size_t)n;
+                    const int rv = rank[v];
+                    lb[v] = umax64(est_first(lsz[off + v], lk[off + v], rv, M),
+                                   est_first(lsz[off + w], lk[off + w], rv, M));
+                    fresh[v] = 0;
+                    my_bytes += 29ull + 9ull;
+                }
+                continue;
+            }
+        }
         if (e - b > kWarpRow) {
             int slot = 0;
             if (lane == 0) slot = atomicAdd(&s_nheavy, 1);
@@ -1577,7 +1599,8 @@ void launch_stale_sampled(Graph& g, const int* list, const int* d_count, cudaStr
     prof_begin(g, kProfFrontier, s);
     k_stale_sampled<<<grid, kLuThreads, 0, s>>>(g.rowptr, g.col, g.alive, g.rank, g.lsz, g.lk, g.h,
                                                 g.hv, g.M, g.Mv, only_h, list, d_count, g.n,
-                                                g.fresh, g.lb64, &g.state->bytes[kProfFrontier]);
+                                                g.fresh, g.lb64, &g.state->bytes[kProfFrontier],
+                                                g.bestnb);
     count_launch(g, 1);
     prof_end(g, kProfFrontier, s);
 }

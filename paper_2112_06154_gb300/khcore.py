@@ -57,6 +57,8 @@ SIGNATURES = [
     ("kh_graph_free", ctypes.c_int, [_P]),
     ("kh_graph_load_batch", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_uint32, _PP]),
     ("kh_graph_n", ctypes.c_int, [_P, _I64P]),
+    ("kh_footprint", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                    ctypes.c_double, ctypes.c_double, _I64P, _I64P]),
     ("kh_set_h", ctypes.c_int, [_P, ctypes.c_int32]),
     ("kh_set_sampling", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_double]),
@@ -360,6 +362,17 @@ def kh_peel_stats(g: Graph):
 
 def kh_sync(g: Graph):
     _check(load().kh_sync(g.handle), g.ctx)
+
+
+def kh_footprint(n: int, nnz: int, h: int, M: int = 0, eps: float = 0.5, delta: float = 0.05):
+    """(M in force, upper bound of device bytes) of a sampled decomposition of a
+    graph of n nodes and nnz adjacency entries, before loading it (host only)."""
+    m = ctypes.c_int64()
+    b = ctypes.c_int64()
+    rc = load().kh_footprint(n, nnz, h, M, eps, delta, ctypes.byref(m), ctypes.byref(b))
+    if rc != KH_OK:
+        raise KhError(rc, "kh_footprint: bad sizes or sampling parameters")
+    return int(m.value), int(b.value)
 
 
 def kh_graph_n(g: Graph) -> int:

@@ -17,7 +17,6 @@ host-side tests drive the admission logic without a GPU.
 """
 from __future__ import annotations
 
-import math
 import threading
 import time
 from collections import deque
@@ -28,21 +27,16 @@ import numpy as np
 
 
 def budget_M(n: int, eps: float, delta: float) -> int:
-    """Eq. (buffer) of the paper: M = floor(1 + 4(2+eps)/eps^2 (log(2n/delta) + log 8))."""
-    return int(math.floor(1.0 + 4.0 * (2.0 + eps) / eps ** 2 *
-                          (math.log(2.0 * max(n, 1) / delta) + math.log(8.0))))
+    """M of Eq. (buffer) as the library computes it (kh_footprint)."""
+    from . import khcore as K
+    return K.kh_footprint(n, 0, 1, 0, eps, delta)[0]
 
 
 def footprint_bytes(n: int, nnz: int, h: int, M: int) -> int:
-    """Device bytes a sampled decomposition holds: the CSR, the per-node work
-    arrays, the level lists of levels 1..h-1 (one slot of M keys per node and
-    level, rounded up to 4 keys) and the per-level sizes."""
-    cap = (M + 3) // 4 * 4
-    csr = 8 * (n + 1) + 4 * nnz
-    per_node = n * 96
-    lists = max(h - 1, 0) * n * cap * 4
-    levels = h * n * 5
-    return csr + per_node + lists + levels + (1 << 20)
+    """The library's upper bound of the device bytes a sampled decomposition of
+    this graph allocates (kh_footprint)."""
+    from . import khcore as K
+    return K.kh_footprint(n, nnz, h, M)[1]
 
 
 @dataclass
