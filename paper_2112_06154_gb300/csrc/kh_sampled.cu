@@ -604,7 +604,7 @@ __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& 
 // FREE: the union's warps run free instead of in barrier-separated steps (see
 // the FREE branch below); both give the same lists.
 template <bool FREE>
-__global__ void __launch_bounds__(kLuThreads) k_levelU(LevelArgs a, int lg) {
+__global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int hcap = 1 << lg;
     uint32_t* tab = s_dyn;
