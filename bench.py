@@ -626,9 +626,12 @@ def run_sweep(args):
     """Analogues of Fig. 1 and Fig. 2 (Sec. 8.2, 8.3), on seeded synthetic graphs.
     (1) eps sweep: M from Eq. (buffer); the sampled (k,h)-core's time and its
     relative error |c'(v) - c(v)| / c(v) against the exact core (maximum, the
-    paper's measure, and mean) on the Chung-Lu n=200k graph (h=2) and a Chung-Lu
-    n=20k graph (h=3).  (2) hierarchical SBM, n = 10k..100k, h = 2, 3, 4 at
-    eps = 0.5: the sampled core's time against the number of edges."""
+    paper's measure, and mean) on the Chung-Lu n=200k graph (h=2), and, as Fig. 1
+    does at h = 3 and 4, on a collaboration-shaped Chung-Lu graph (n = 18k, mean
+    degree 21) and a co-purchase-shaped one (n = 100k, mean degree 5.5, exponent
+    2.8); eps goes down to 0.12, where M reaches 12000, the largest hash set a
+    CTA's shared memory holds.  (2) hierarchical SBM, n = 10k..100k, h = 2, 3, 4
+    at eps = 0.5: the sampled core's time against the number of edges."""
     import torch
     from paper_2112_06154_gb300 import graphgen as gg
     from paper_2112_06154_gb300 import khcore as K
@@ -644,9 +647,13 @@ def run_sweep(args):
 
     out = {"workload": "eps_sweep_and_sbm", "impl": "ours", "unit": "s", "higher_is_better": False,
            "eps_sweep": [], "sbm": []}
+    collab = gg.chung_lu(18000, 21, 2.5, 1000, 1102)
+    copurchase = gg.chung_lu(100000, 5.5, 2.8, 300, 1103)
     cases = [("chung_lu_n200k", Workload("chung_lu").make_graph(), 2, (0.5, 0.35, 0.25)),
-             ("chung_lu_n20k", gg.chung_lu(20000, 20, 2.5, 1000, 1102), 3,
-              (0.5, 0.4, 0.3, 0.2, 0.15))]
+             ("collab_n18k", collab, 3, (0.5, 0.4, 0.3, 0.2, 0.15, 0.12)),
+             ("collab_n18k", collab, 4, (0.5, 0.4, 0.3, 0.2, 0.15, 0.12)),
+             ("copurchase_n100k", copurchase, 3, (0.5, 0.4, 0.3, 0.2, 0.15)),
+             ("copurchase_n100k", copurchase, 4, (0.5, 0.4, 0.3, 0.2))]
     for name, (rowptr, col), h, eps_list in cases:
         G = K.kh_graph_load_csr(ctx, rowptr, col)
         K.kh_set_h(G, h)
@@ -692,7 +699,7 @@ def run_batch(args):
       sampled: Core (Alg. 4) on all graphs at their own h;
       exact:   ExactCore at h = 2 on the first --exact-graphs graphs (exact
                peels at h = 3, 4 of these graphs are the O(n^2 m) regime the
-               paper's sampling exists to avoid; see the design notes)."""
+               paper's sampling exists to avoid)."""
     import torch
     from paper_2112_06154_gb300 import graphgen as gg
     from paper_2112_06154_gb300 import khcore as K
