@@ -291,8 +291,8 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
  * trim) schedules a node's lists over the warps of its CTA.
  * KH_LEVELU_STEPPED: barrier-separated steps, the trim once per step;
  * KH_LEVELU_FREE: warps claim lists and trim from their own view of the rank
- * counts, meeting only to compact the hash set.  KH_VAR_AUTO: stepped.  The
- * lists are the same either way. */
+ * counts, meeting only to compact the hash set.  KH_VAR_AUTO: free (the
+ * faster on every measured graph).  The lists are the same either way. */
 #define KH_OP_LEVEL_UNION 2
 #define KH_LEVELU_STEPPED 1
 #define KH_LEVELU_FREE 2

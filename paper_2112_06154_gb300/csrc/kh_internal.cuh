@@ -331,7 +331,7 @@ struct Graph {
     const int32_t *vlist;
     int64_t vcount;
     int compact_mode;       // KH_VAR_AUTO, KH_COMPACT_OFF or KH_COMPACT_ALWAYS
-    int levelu_mode;        // KH_VAR_AUTO (stepped), KH_LEVELU_STEPPED or KH_LEVELU_FREE
+    int levelu_mode;        // KH_VAR_AUTO (free), KH_LEVELU_STEPPED or KH_LEVELU_FREE
     int cp_cur;             // buffer set in use (0 or 1)
     int64_t *cp_row[2];
     int32_t *cp_col[2];

@@ -1521,7 +1521,9 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
     const size_t dyn = levelU_smem(lg);
-    void (*kern)(LevelArgs, int) = g.levelu_mode == KH_LEVELU_FREE ? k_levelU<true> : k_levelU<false>;
+    // free-running warps unless the stepped schedule is asked for (free is the
+    // faster one on every measured workload)
+    void (*kern)(LevelArgs, int) = g.levelu_mode == KH_LEVELU_STEPPED ? k_levelU<false> : k_levelU<true>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
     int per_sm = 0;
