@@ -161,12 +161,13 @@ def parse():
     p.add_argument("--op", choices=["hdeg2", "hdeg3", "counts2", "est2", "est3", "est4",
                                     "sampled2", "sampled3", "sampled4", "exact2"],
                    help="run one operation once on the workload's graph (a target for profilers)")
-    p.add_argument("--workload", choices=["rmat", "chung_lu", "rmat_ops", "batch", "serve",
-                                          "dense", "sweep"],
+    p.add_argument("--workload", choices=["rmat", "chung_lu", "rmat_ops", "c2_ops", "batch",
+                                          "serve", "dense", "sweep"],
                    default="rmat",
-                   help="rmat (default) / chung_lu: headline step; rmat_ops: single operations on "
-                        "R-MAT 22; batch: 4096 preferential-attachment graphs, batched vs one graph "
-                        "per call; serve: a Poisson request stream through the server")
+                   help="rmat (default) / chung_lu: headline step; rmat_ops / c2_ops: single "
+                        "operations on R-MAT 22 / Chung-Lu 200k; batch: 4096 preferential-attachment "
+                        "graphs, batched vs one graph per call; serve: a Poisson request stream "
+                        "through the server")
     p.add_argument("--rmat-scale", type=int, default=22,
                    help="--op only: R-MAT scale of the graph (a smaller case for profilers)")
     p.add_argument("--variant", default=None,
@@ -533,26 +534,33 @@ def run_op(args):
     ctx.close()
 
 
-def run_rmat_ops(args):
-    """R-MAT scale 22 (a=.57, b=c=.19, 16 edges per node generated, symmetrised,
-    deduplicated): exact h-degrees at h=2, adaptive estimates and sampled
-    (k,h)-cores at h=2,3,4, each timed once after a warm-up load."""
+def run_ops(args):
+    """Single operations on one graph, each timed once after a warm-up call:
+    rmat_ops: R-MAT scale 22: exact h-degrees at h=2, adaptive estimates and
+              sampled (k,h)-cores at h=2,3,4;
+    c2_ops:   Chung-Lu n=200k: exact h-degrees, fixed-level counts and estimates
+              at h=2,3, sampled cores at h=2,3,4 and exact cores at h=2,3."""
     import torch
     from paper_2112_06154_gb300 import graphgen as gg
     from paper_2112_06154_gb300 import khcore as K
     K.load()
+    rmat = args.workload == "rmat_ops"
     t0 = time.perf_counter()
-    rowptr, col = gg.rmat(22, 16, 0.57, 0.19, 0.19, 1003)
+    rowptr, col = (gg.rmat(22, 16, 0.57, 0.19, 0.19, 1003) if rmat
+                   else Workload("chung_lu").make_graph())
     stats = gg.graph_stats(rowptr, col)
     gen_s = time.perf_counter() - t0
     ctx = K.kh_ctx_create(0)
     G = K.kh_graph_load_csr(ctx, rowptr, col)
     K.kh_set_sampling(G, seed=1)
     apply_union(K, G, args)
-    out = {"workload": "rmat_scale22_ops", "impl": "ours", "union": args.union, "graph": stats, "M": K.kh_get_M(G),
-           "gen_s": gen_s, "unit": "s", "higher_is_better": False}
+    out = {"workload": "rmat_scale22_ops" if rmat else "chung_lu_n200k_ops", "impl": "ours",
+           "union": args.union, "graph": stats, "M": K.kh_get_M(G), "gen_s": gen_s, "unit": "s",
+           "higher_is_better": False}
 
-    def timed(fn):
+    def timed(fn, warm=False):
+        if warm:
+            fn()
         torch.cuda.synchronize()
         t = time.perf_counter()
         r = fn()
@@ -566,15 +574,28 @@ def run_rmat_ops(args):
     ms, _, b = K.kh_prof_read(G, K.KH_PROF_BFS)
     K.kh_prof_enable(G, False)
     out["hdeg_h2_alg_GBps"] = b / 1e6 / ms if ms > 0 else None
+    if not rmat:
+        K.kh_set_h(G, 3)
+        _, out["hdeg_h3_s"] = timed(lambda: K.kh_hdegree_exact(G), True)
+        for h in (2, 3):
+            K.kh_set_h(G, h)
+            _, out[f"counts_h{h}_s"] = timed(lambda: K.kh_sampled_counts(G, J_LO, J_HI), True)
     for h in (2, 3, 4):
         K.kh_set_h(G, h)
-        _, out[f"estimate_h{h}_s"] = timed(lambda: K.kh_estimate(G))
+        _, out[f"estimate_h{h}_s"] = timed(lambda: K.kh_estimate(G), not rmat)
     for h in (2, 3, 4):
         K.kh_set_h(G, h)
-        core, secs = timed(lambda: K.kh_core_sampled(G))
+        core, secs = timed(lambda: K.kh_core_sampled(G), not rmat)
         _, rounds, updates = K.kh_peel_info(G, False)
         out[f"core_sampled_h{h}"] = {"s": secs, "rounds": rounds, "updates": updates,
                                      "max_core": int(core.max())}
+    if not rmat:
+        for h in (2, 3):
+            K.kh_set_h(G, h)
+            core, secs = timed(lambda: K.kh_core_exact(G), h == 2)
+            _, rounds, updates = K.kh_peel_info(G, False)
+            out[f"core_exact_h{h}"] = {"s": secs, "rounds": rounds, "updates": updates,
+                                       "max_core": int(core.max()), "us_per_round": 1e6 * secs / rounds}
     free, total = torch.cuda.mem_get_info()
     out["device_gib_used"] = (total - free) / 2**30
     print(json.dumps(out), flush=True)
@@ -841,8 +862,8 @@ def main():
         run_serve(args)
     elif args.workload == "batch" and args.impl == "ours":
         run_batch(args)
-    elif args.workload == "rmat_ops" and args.impl == "ours":
-        run_rmat_ops(args)
+    elif args.workload in ("rmat_ops", "c2_ops") and args.impl == "ours":
+        run_ops(args)
     elif args.workload == "dense" and args.impl == "ours":
         run_dense(args)
     elif args.workload == "sweep" and args.impl == "ours":
