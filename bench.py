@@ -171,8 +171,9 @@ def parse():
     p.add_argument("--rmat-scale", type=int, default=22,
                    help="--op only: R-MAT scale of the graph (a smaller case for profilers)")
     p.add_argument("--variant", default=None,
-                   help="--op hdeg2/counts2 only: force the 2-degree layout, 'cta' or 'sliced,S,T'")
-    p.add_argument("--union", choices=["auto", "stepped", "free"], default="auto",
+                   help="--op hdeg2/counts2 only: force the 2-degree layout: 'cta', 'sliced,S,T' or "
+                        "'small,S,T' (sliced, small balls one warp each)")
+    p.add_argument("--union", choices=["auto", "stepped", "free", "grouped"], default="auto",
                    help="schedule of the level-union kernel (kh_set_variant KH_OP_LEVEL_UNION)")
     p.add_argument("--prof", action="store_true",
                    help="--op only: bracket the kernel classes and print their times and "
@@ -188,7 +189,8 @@ def parse():
 
 
 def apply_union(K, G, args):
-    mode = {"auto": K.KH_VAR_AUTO, "stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE}
+    mode = {"auto": K.KH_VAR_AUTO, "stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE,
+            "grouped": K.KH_LEVELU_GROUPED}
     K.kh_set_variant(G, mode[getattr(args, "union", "auto")], op=K.KH_OP_LEVEL_UNION)
 
 
@@ -509,7 +511,8 @@ def run_op(args):
         if f[0] == "cta":
             K.kh_set_variant(G, K.KH_VAR_CTA)
         else:
-            K.kh_set_variant(G, K.KH_VAR_SLICED, int(f[1]), int(f[2]))
+            var = K.KH_VAR_SLICED_SMALL if f[0] == "small" else K.KH_VAR_SLICED
+            K.kh_set_variant(G, var, int(f[1]), int(f[2]))
     if args.prof:
         K.kh_prof_enable(G, True)
     t0 = time.perf_counter()

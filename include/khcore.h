@@ -279,6 +279,10 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
 #define KH_VAR_AUTO 0
 #define KH_VAR_CTA 1
 #define KH_VAR_SLICED 2
+/* KH_VAR_SLICED_SMALL: as KH_VAR_SLICED for sources whose 2-hop work (the sum
+ * of their neighbours' degrees) is at least 511; the others take one warp
+ * each with a private hash set of their 2-ball in shared memory. */
+#define KH_VAR_SLICED_SMALL 3
 /* KH_OP_PEEL_COMPACT: the peels (kh_core_*, kh_dense*) switch, each time the
  * alive node count has halved, to a CSR that keeps only the neighbours alive
  * at that moment (node ids unchanged; results unchanged).  KH_VAR_AUTO: for
@@ -291,11 +295,16 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
  * trim) schedules a node's lists over the warps of its CTA.
  * KH_LEVELU_STEPPED: barrier-separated steps, the trim once per step;
  * KH_LEVELU_FREE: warps claim lists and trim from their own view of the rank
- * counts, meeting only to compact the hash set.  KH_VAR_AUTO: free (the
- * faster on every measured graph).  The lists are the same either way. */
+ * counts, meeting only to compact the hash set;
+ * KH_LEVELU_GROUPED: as free, with groups of 32, 16, ..., 1 lanes claiming
+ * lists in place of whole warps: per node, the fewest lanes whose step of
+ * 4 keys a lane covers the keys a list is expected to give at or above the
+ * starting level (sum of |B[w]| 2^(k[w] - t) over the lists, over their
+ * number).  KH_VAR_AUTO: grouped.  The lists are the same every way. */
 #define KH_OP_LEVEL_UNION 2
 #define KH_LEVELU_STEPPED 1
 #define KH_LEVELU_FREE 2
+#define KH_LEVELU_GROUPED 3
 int kh_set_variant(kh_graph *g, int32_t op, int32_t variant, int32_t slices, int32_t threads);
 int kh_get_variant(kh_graph *g, int32_t op, int32_t *variant, int32_t *slices, int32_t *threads,
                    double *tuned_ms);

@@ -26,7 +26,7 @@ namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kMaxHeavy2 = 128;      // rows expanded by the whole CTA per item
-constexpr int kHeavyRow2 = 2048;     // a row part this long goes to the whole CTA
+constexpr int kHeavyRow2 = 512;      // a row part this long goes to the whole CTA
 constexpr int kTouchCap = 4096;      // words cleared one by one (else full clear)
 constexpr int kOrderBins = 48;       // log2 bins of the 2-hop work
 
@@ -53,21 +53,23 @@ struct Slice2Args {
 // entries and keeps the gap where the sorted row crosses key.
 __device__ __forceinline__ int64_t warp_lower_bound(const int32_t* __restrict__ col, int64_t b,
                                                     int64_t e, int32_t key, int lane) {
-    int64_t lo = b, hi = e;  // answer in [lo, hi]
+    // 32-bit offsets from b (a row has fewer than 2^31 entries)
+    const int32_t* __restrict__ r = col + b;
+    int lo = 0, hi = (int)(e - b);  // answer in [lo, hi]
     while (hi - lo > 32) {
-        const int64_t step = (hi - lo + 31) / 32;
-        const int64_t p = lo + (int64_t)lane * step;
-        const bool below = p < hi && __ldg(col + p) < key;
+        const int step = (hi - lo + 31) >> 5;
+        const int p = lo + lane * step;
+        const bool below = p < hi && __ldg(r + p) < key;
         const int c = __popc(__ballot_sync(kFull, below));
         // positions lo + j*step, j < c, hold keys below `key`
-        const int64_t nlo = c > 0 ? lo + (int64_t)(c - 1) * step + 1 : lo;
-        const int64_t nhi = lo + (int64_t)c * step;
+        const int nlo = c > 0 ? lo + (c - 1) * step + 1 : lo;
+        const int nhi = lo + c * step;
         lo = nlo;
         hi = nhi < hi ? nhi : hi;
     }
-    const int64_t p = lo + lane;
-    const bool below = p < hi && __ldg(col + p) < key;
-    return lo + __popc(__ballot_sync(kFull, below));
+    const int p = lo + lane;
+    const bool below = p < hi && __ldg(r + p) < key;
+    return b + lo + __popc(__ballot_sync(kFull, below));
 }
 
 // Mark u (in the slice) in the bitmap; count it and remember its word when it
@@ -110,14 +112,17 @@ __device__ __forceinline__ void mark_range(const Slice2Args& a, uint32_t* bm, in
                                            int* s_ntouch, int* s_hist, int64_t ps, int64_t pe,
                                            int64_t first, int64_t stride, int32_t lo, int lane,
                                            int& my) {
-    for (int64_t k0 = ps + first; k0 < pe; k0 += stride) {
+    // 32-bit offsets from the part's start (a row has fewer than 2^31 entries)
+    const int32_t* __restrict__ base = a.col + ps;
+    const int len = (int)(pe - ps);
+    for (int k0 = (int)first; k0 < len; k0 += (int)stride) {
         int32_t u[4];
         bool val[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int64_t k = k0 + q * 32 + lane;
-            val[q] = k < pe;
-            u[q] = val[q] ? __ldg(a.col + k) : lo;
+            const int k = k0 + q * 32 + lane;
+            val[q] = k < len;
+            u[q] = val[q] ? __ldg(base + k) : lo;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -131,7 +136,7 @@ __global__ void k_hdeg2_slice(Slice2Args a) {
     const int words = (int)(a.width >> 5);
     uint32_t* bm = s_dyn;
     int32_t* touch = reinterpret_cast<int32_t*>(s_dyn + words);
-    __shared__ int s_item, s_ntouch, s_nheavy, s_count;
+    __shared__ int s_item, s_ntouch, s_nheavy, s_count, s_row;
     __shared__ int64_t s_hb[kMaxHeavy2], s_he[kMaxHeavy2];
     __shared__ int s_hist[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -147,6 +152,7 @@ __global__ void k_hdeg2_slice(Slice2Args a) {
             s_item = atomicAdd(a.work_ctr, 1);
             s_ntouch = 0;
             s_nheavy = 0;
+            s_row = 0;
             s_count = 0;
         }
         if (RANKS && tid < 32) s_hist[tid] = 0;
@@ -161,8 +167,13 @@ __global__ void k_hdeg2_slice(Slice2Args a) {
         const int64_t vb = a.rowptr[v], ve = a.rowptr[v + 1];
         const int64_t deg = ve - vb;
         int my = 0;
-        // rows: v's own (i == deg) and each neighbour's (i < deg)
-        for (int64_t i = warp; i <= deg; i += nwarps) {
+        // rows: v's own (i == deg) and each neighbour's (i < deg), claimed by
+        // the warps one at a time (row lengths vary widely)
+        for (;;) {
+            int64_t i = 0;
+            if (lane == 0) i = atomicAdd(&s_row, 1);
+            i = __shfl_sync(kFull, i, 0);
+            if (i > deg) break;
             const int32_t x = i < deg ? __ldg(a.col + vb + i) : v;
             const int64_t rb = a.rowptr[x], re = a.rowptr[x + 1];
             const int64_t ps = lo > 0 ? warp_lower_bound(a.col, rb, re, lo, lane) : rb;
@@ -214,6 +225,87 @@ __global__ void k_hdeg2_slice(Slice2Args a) {
     }
     for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
     if (lane == 0 && my_bytes) atomicAdd(a.bytes, my_bytes);
+}
+
+// Sources of small 2-hop work (bin < kSmallBin: work < 2^kSmallBin, so at most
+// 2 (2^kSmallBin - 1) row entries in all) take one warp each, without slices:
+// the warp dedupes its source's 2-ball in a private open-addressing set of
+// kSmallSlots node ids in shared memory (load at most one half), cleared with
+// vector stores afterwards.  This spares the per-item cost of S slice items
+// for the many small balls of a power-law graph.
+constexpr int kSmallBin = 9;
+constexpr int kSmallSlots = 2048;
+constexpr int kSmallWarps = 8;
+constexpr uint32_t kIdEmpty = 0xffffffffu;
+
+template <bool RANKS>
+__global__ void __launch_bounds__(kSmallWarps * 32)
+    k_hdeg2_small(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const uint8_t* __restrict__ rank, const int32_t* __restrict__ order,
+                  int64_t count, int32_t* __restrict__ deg, int32_t* __restrict__ cnt, int jlo,
+                  int nj, unsigned long long* updates, unsigned long long* bytes) {
+    extern __shared__ __align__(16) uint32_t s_tab_all[];
+    __shared__ int s_hist_all[kSmallWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tab = s_tab_all + (size_t)warp * kSmallSlots;
+    int* hist = s_hist_all[warp];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long my_bytes = 0, my_upd = 0;
+    {
+        uint4* t4 = reinterpret_cast<uint4*>(tab);
+        for (int i = lane; i < kSmallSlots / 4; i += 32) t4[i] = make_uint4(kIdEmpty, kIdEmpty, kIdEmpty, kIdEmpty);
+    }
+    __syncwarp();
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nw) {
+        const int v = order[i];
+        if (RANKS) hist[lane] = 0;
+        __syncwarp();
+        const int64_t vb = rowptr[v], ve = rowptr[v + 1];
+        const int64_t dv = ve - vb;
+        int my = 0;
+        // rows: v's own (r == dv) and each neighbour's
+        for (int64_t r = 0; r <= dv; ++r) {
+            const int32_t x = r < dv ? __ldg(col + vb + r) : v;
+            const int64_t rb = rowptr[x], re = rowptr[x + 1];
+            if (lane == 0) my_bytes += 8ull + 4ull * (unsigned long long)(re - rb);
+            for (int64_t k = rb + lane; k < re; k += 32) {
+                const uint32_t u = (uint32_t)__ldg(col + k);
+                uint32_t slot = (u * 0x9E3779B1u) >> (32 - 11);  // 2^11 = kSmallSlots
+                for (int probe = 0; probe < kSmallSlots; ++probe) {
+                    const uint32_t cur = *(volatile uint32_t*)(tab + slot);
+                    if (cur == u) break;
+                    if (cur == kIdEmpty) {
+                        const uint32_t prev = atomicCAS(tab + slot, kIdEmpty, u);
+                        if (prev == kIdEmpty) {
+                            ++my;
+                            if (RANKS) atomicAdd(&hist[rank[u]], 1);
+                            break;
+                        }
+                        if (prev == u) break;
+                    }
+                    slot = (slot + 1u) & (kSmallSlots - 1);
+                }
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(kFull, my, off);
+        __syncwarp();
+        if (lane == 0) {
+            deg[v] = my - 1;  // the ball holds v itself (by symmetry, in each neighbour's row)
+            ++my_upd;
+            my_bytes += 4ull + (RANKS ? 4ull * (unsigned long long)nj : 0ull);
+        }
+        if (RANKS && lane < nj) {
+            int c = 0;
+            for (int j = jlo + lane; j < 32; ++j) c += hist[j];
+            cnt[(size_t)v * nj + lane] = c - (rank[v] >= jlo + lane ? 1 : 0);
+        }
+        uint4* t4 = reinterpret_cast<uint4*>(tab);
+        for (int q = lane; q < kSmallSlots / 4; q += 32) t4[q] = make_uint4(kIdEmpty, kIdEmpty, kIdEmpty, kIdEmpty);
+        __syncwarp();
+    }
+    for (int off = 16; off > 0; off >>= 1) my_bytes += __shfl_down_sync(kFull, my_bytes, off);
+    if (lane == 0 && my_bytes) atomicAdd(bytes, my_bytes);
+    if (lane == 0 && my_upd) atomicAdd(updates, my_upd);
 }
 
 // 2-hop work of each node and its log2 bin (isolated nodes: bin -1).
@@ -320,6 +412,7 @@ int ensure_order2(Graph& g, cudaStream_t s) {
             acc += h[b];
         }
         g.nsrc2 = acc;
+        for (int b = 0; b < kOrderBins; ++b) g.order2_hist[b] = h[b];
         e = cudaMemcpyAsync(hist, pos, sizeof(pos), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) {
             k_order_scatter<<<grid, 256, 0, s>>>(bin, g.n, hist, g.order2);
@@ -334,6 +427,34 @@ int ensure_order2(Graph& g, cudaStream_t s) {
         g.order2 = nullptr;
         return check_cuda(g.ctx, e, "source order");
     }
+    return KH_OK;
+}
+
+int64_t hdeg2_small_split(const Graph& g) {
+    int64_t big = 0;
+    for (int b = kSmallBin; b < kOrderBins; ++b) big += g.order2_hist[b];
+    return big;
+}
+
+int launch_hdeg2_small(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
+                       const int32_t* order, int64_t count) {
+    if (count <= 0) return KH_OK;
+    void (*kern)(const int64_t*, const int32_t*, const uint8_t*, const int32_t*, int64_t, int32_t*,
+                 int32_t*, int, int, unsigned long long*, unsigned long long*) =
+        cnt ? k_hdeg2_small<true> : k_hdeg2_small<false>;
+    const size_t dyn = (size_t)kSmallWarps * kSmallSlots * 4;
+    KH_CUDA_TRY(g.ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    KH_CUDA_TRY(g.ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallWarps * 32, dyn));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)g.ctx->sm_count * per_sm;
+    const int64_t need = (count + kSmallWarps - 1) / kSmallWarps;
+    if (grid > need) grid = need;
+    prof_begin(g, kProfBfs, s);
+    kern<<<(int)grid, kSmallWarps * 32, dyn, s>>>(g.rowptr, g.col, g.rank, order, count, deg, cnt, jlo,
+                                                   nj, &g.state->updates, &g.state->bytes[kProfBfs]);
+    count_launch(g, 1);
+    prof_end(g, kProfBfs, s);
     return KH_OK;
 }
 

@@ -45,6 +45,7 @@ constexpr int kErrQueue = 1;   // BFS queue overflow
 constexpr int kErrProbe = 2;   // hash probe limit reached
 constexpr int kErrList = 4;    // list larger than its slot
 constexpr int kErrGraph = 8;   // CSR validation failure
+constexpr int kErrLoop = 16;   // a work loop ran past its iteration bound
 
 // Kernel classes for the profiling counters (kh_prof_read kinds).
 constexpr int kProfBfs = 0;       // exact h-degree / fixed-level count BFS
@@ -162,6 +163,11 @@ int launch_hdeg2_slice(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cu
 // the sources of the sliced kernel, longest 2-hop work first (cached per graph)
 int ensure_order2(Graph& g, cudaStream_t s);
 size_t hdeg2_smem(int64_t width);
+// sources of order2 whose 2-hop work is too large for the warp-per-source
+// kernel (they come first in order2), and that kernel for the rest
+int64_t hdeg2_small_split(const Graph& g);
+int launch_hdeg2_small(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
+                       const int32_t* order, int64_t count);
 // kh_tune.cu: the layout of the 2-degree pass for this graph (tuned once), and
 // the whole-graph exact h-degree / fixed-level count pass through it
 int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out);
@@ -331,7 +337,7 @@ struct Graph {
     const int32_t *vlist;
     int64_t vcount;
     int compact_mode;       // KH_VAR_AUTO, KH_COMPACT_OFF or KH_COMPACT_ALWAYS
-    int levelu_mode;        // KH_VAR_AUTO (free), KH_LEVELU_STEPPED or KH_LEVELU_FREE
+    int levelu_mode;        // KH_VAR_AUTO (grouped), KH_LEVELU_STEPPED, _FREE or _GROUPED
     int cp_cur;             // buffer set in use (0 or 1)
     int64_t *cp_row[2];
     int32_t *cp_col[2];
@@ -342,6 +348,7 @@ struct Graph {
     // sliced 2-degree kernel: sources longest first (non-isolated nodes only)
     int32_t *order2;
     int64_t nsrc2;
+    int64_t order2_hist[48];  // sources per log2 bin of 2-hop work (order2 is by descending bin)
     // each node's neighbour of largest degree (-1: none), for cheap stale bounds
     int32_t *bestnb;
     // the 2-degree pass layout: forced by kh_set_variant, or chosen by the tuner

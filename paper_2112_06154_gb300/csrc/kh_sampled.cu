@@ -57,6 +57,7 @@ struct LevelArgs {
     const int* d_count;
     int64_t count_static;
     int track;
+    int group_lists;           // free union: lanes per list by the list count (else a warp)
     int32_t* changed;
     int* n_changed;
     int32_t* heavy;            // level 1: nodes of degree > kL1Heavy, for the CTA kernel
@@ -464,15 +465,18 @@ __device__ __forceinline__ int snapshot_counts(const int* s_hist, int lane) {
     return S;
 }
 
-// The union of free-running warps (k_levelU<true>): each warp claims whole
-// lists from a shared counter and reads each in 128-key chunks (four keys per
-// lane) until a key below the running level t shows (lists are grouped by
-// rank, highest first).  After every chunk the warp raises t from its
-// snapshot of the rank counts (Alg. 5's trim) and, in a refine, tests the
-// partial estimate against T.  The CTA meets at a barrier only to compact the
-// set (once it holds more than half its slots: at most one chunk per warp
-// and one more from each other warp follow before they stop, so the set
-// never fills) and at the end, where warp 0 trims from the complete counts.
+// The union of free-running warps (k_levelU<true>): the warps' lanes form
+// groups of G (G = 32: a warp per list); each group claims whole lists from a
+// shared counter and reads its list 4 G keys per step (four keys per lane)
+// until a key below the running level t shows (lists are grouped by rank,
+// highest first).  After every step the warp raises t from its snapshot of
+// the rank counts (Alg. 5's trim) and, in a refine, tests the partial
+// estimate against T.  The CTA meets at a barrier only to compact the set
+// (once it holds more than half its slots: at most one step per warp and one
+// more from each other warp follow before they stop, so the set never fills)
+// and at the end, where warp 0 trims from the complete counts.  Small groups
+// suit many lists that each give a few keys above t: a warp step then covers
+// 32 / G lists instead of one.
 // Returns true when the refine stopped early (s_part holds the bound).
 __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& nl, uint32_t* tab,
                                         uint32_t* stage, uint16_t* used, int lg, int hcap,
@@ -480,46 +484,77 @@ __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& 
                                         int* s_exit, unsigned long long* s_part, int* s_item,
                                         int* s_creq, unsigned long long T, int vin, bool can_stop,
                                         int mode, int first, int64_t b, int l0, int L, int rv,
-                                        unsigned long long& my_bytes) {
+                                        int G, unsigned long long& my_bytes) {
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
         *s_item = 0;
         *s_creq = 0;
     }
     __syncthreads();
-    int cli = -1, cpos = 0, csz = 0;  // this warp's open list (kept across a compaction)
+    // this group's open list (kept across a compaction): index (-1: none,
+    // -2: the last claim found no list left), position, size
+    int cli = -1, cpos = 0, csz = 0;
     const uint32_t* clp = nullptr;
+    // every step claims a list or reads 4 keys of one: a bound on the steps
+    // that no correct run reaches (past it: error flag, and the union ends)
+    const long long cap64 = (long long)L * ((long long)a.cap / 4 + 2) + 4096;
+    int steps_left = cap64 < 0x7fffffffLL ? (int)cap64 : 0x7fffffff;
     for (;;) {
         for (;;) {
-            if (*(volatile int*)s_creq || *(volatile int*)s_exit) break;
-            if (cli < 0) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(s_item, 1);
-                c = __shfl_sync(kFull, c, 0);
-                if (c >= L) break;
-                cli = l0 + c;
-                cpos = 0;
-                csz = 0;
-                if (mode == 2) {
-                    csz = __ldcg(a.part_size + first + cli);
-                    clp = a.part_keys + (size_t)(first + cli) * (size_t)a.cap;
-                } else {
-                    const int32_t w = a.col[b + cli];
-                    // a list whose highest rank is below t has nothing to give
-                    if (a.alive[w] == 1 && (int)nl.ltop_in[w] >= *(volatile int*)s_t) {
-                        csz = min(nl.lsz_in[w], (int)a.cap);
-                        clp = nl.keys_in + (size_t)w * (size_t)a.cap;
+            // one read for the whole warp: lanes that saw the flags at different
+            // moments would leave the loop apart and stall the warp's shuffles
+            int stop = 0;
+            if (lane == 0) stop = *(volatile int*)s_creq | *(volatile int*)s_exit;
+            if (__shfl_sync(kFull, stop, 0)) break;
+            if (--steps_left < 0) {
+                if (lane == 0) {
+                    atomicOr(a.err, kErrLoop);
+                    atomicCAS(s_exit, 0, 3);
+                }
+                break;
+            }
+            // groups without an open list claim the next lists (a list that
+            // turns out dead, or with nothing at or above t, is passed over)
+            for (int tries = 0; tries < 4; ++tries) {
+                const bool need = cli == -1;
+                const uint32_t nb = __ballot_sync(kFull, need && (lane & (G - 1)) == 0);
+                if (!nb) break;
+                const int lead = __ffs(nb) - 1;
+                int base = 0;
+                if (lane == lead) base = atomicAdd(s_item, __popc(nb));
+                base = __shfl_sync(kFull, base, lead);
+                int c = base + __popc(nb & ((1u << lane) - 1u)), sz = 0, w = -1;
+                if (need && (lane & (G - 1)) == 0 && c < L) {
+                    if (mode == 2) {
+                        sz = __ldcg(a.part_size + first + c);
+                    } else {
+                        w = a.col[b + l0 + c];
+                        // a list whose highest rank is below t has nothing to give
+                        if (a.alive[w] == 1 && (int)nl.ltop_in[w] >= *(volatile int*)s_t)
+                            sz = min(nl.lsz_in[w], (int)a.cap);
                     }
                 }
-                if (cpos >= csz) {
-                    cli = -1;
-                    continue;
+                const int src = lane & ~(G - 1);
+                c = __shfl_sync(kFull, c, src);
+                sz = __shfl_sync(kFull, sz, src);
+                w = __shfl_sync(kFull, w, src);
+                if (need) {
+                    if (c >= L) {
+                        cli = -2;
+                    } else if (sz > 0) {
+                        cli = l0 + c;
+                        cpos = 0;
+                        csz = sz;
+                        clp = mode == 2 ? a.part_keys + (size_t)(first + c) * (size_t)a.cap
+                                        : nl.keys_in + (size_t)w * (size_t)a.cap;
+                    }
                 }
             }
+            if (__all_sync(kFull, cli == -2)) break;
             const int t = *(volatile int*)s_t;
-            const int p = cpos + lane * kKeysPerLane;
             bool below = false;
-            if (p < csz) {
+            const int p = cpos + (lane & (G - 1)) * kKeysPerLane;
+            if (cli >= 0 && p < csz) {
                 const uint4 k4 = mode == 2 ? __ldcg(reinterpret_cast<const uint4*>(clp + p))
                                            : *reinterpret_cast<const uint4*>(clp + p);
                 const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
@@ -543,9 +578,13 @@ __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& 
                     }
                 }
             }
-            cpos += kChunkKeys;
             // ranks only fall along a list: after a key below t the rest is below t
-            if (__any_sync(kFull, below) || cpos >= csz) cli = -1;
+            const uint32_t bal = __ballot_sync(kFull, below);
+            if (cli >= 0) {
+                const uint32_t gmask = G == 32 ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+                cpos += kKeysPerLane * G;
+                if ((bal & gmask) || cpos >= csz) cli = -1;
+            }
             // trim from this warp's snapshot; the early-stop test in a refine
             const int S = snapshot_counts(s_hist, lane);
             const uint32_t over = __ballot_sync(kFull, S > nl.M);
@@ -615,6 +654,7 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
     __shared__ int s_vin, s_exit;                // own key in the table; early stop taken
     __shared__ int s_rho, s_last;
     __shared__ int s_item, s_creq;              // free mode: list claims; compaction request
+    __shared__ float s_ex;                      // grouped free mode: expected keys x 2^t
     __shared__ unsigned long long s_T, s_part;  // early-stop threshold; partial estimate
     // flat mode (degree <= kFlatMax): per neighbour list its node, size, first
     // chunk index (exclusive prefix of 128-key chunk counts) and the first
@@ -671,6 +711,7 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
             if (tid < 32) s_hist[tid] = 0;
             if (tid == 0) {
                 s_t = 0;
+                s_ex = 0.f;
                 s_nused = 0;
                 s_vin = 0;
                 s_exit = 0;
@@ -686,17 +727,31 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
             const bool can_stop = s_T != ~0ull;
             // t starts at max k[w,i-1] over alive neighbours (Prop. 3.1), or at
             // the largest level of the partial sets (merge)
+            // (grouped free union) also sum |B[w]| 2^k[w]: over 2^t it is the
+            // expected number of keys at or above t (ranks halve per level)
             int myk = 0;
+            float ex = 0.f;
             for (int li = l0 + tid; li < l1; li += blockDim.x) {
+                int k = 0, sz = 0;
                 if (mode == 2) {
-                    myk = max(myk, (int)__ldcg(a.part_t + first + li));
+                    k = (int)__ldcg(a.part_t + first + li);
+                    sz = FREE && a.group_lists ? __ldcg(a.part_size + first + li) : 0;
                 } else {
                     const int32_t w = a.col[b + li];
-                    if (a.alive[w] == 1) myk = max(myk, (int)nl.lk_in[w]);
+                    if (a.alive[w] == 1) {
+                        k = (int)nl.lk_in[w];
+                        sz = FREE && a.group_lists ? min(nl.lsz_in[w], (int)a.cap) : 0;
+                    }
                 }
+                myk = max(myk, k);
+                ex += (float)sz * (float)(1u << (k & 31));
             }
-            for (int off = 16; off > 0; off >>= 1) myk = max(myk, __shfl_down_sync(kFull, myk, off));
+            for (int off = 16; off > 0; off >>= 1) {
+                myk = max(myk, __shfl_down_sync(kFull, myk, off));
+                ex += __shfl_down_sync(kFull, ex, off);
+            }
             if (lane == 0 && myk) atomicMax(&s_t, myk);
+            if (lane == 0 && ex > 0.f) atomicAdd(&s_ex, ex);
             __syncthreads();
             if (tid == 0 && rv >= s_t) {
                 const int slot = set_insert(tab, lg, ((uint32_t)rv << kIdBits) | (uint32_t)v, a.err);
@@ -709,9 +764,17 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
             __syncthreads();
             bool stopped = false;
             if constexpr (FREE) {
+                // lanes per list: a warp, or (grouped) the fewest whose step of
+                // 4 G keys covers the keys a list is expected to give at or
+                // above the starting level
+                int G = 32;
+                if (a.group_lists) {
+                    const float per = s_ex / (float)(1u << (s_t & 31)) / (float)(L > 0 ? L : 1);
+                    while (G > 1 && (float)(kKeysPerLane * (G >> 1)) >= per) G >>= 1;
+                }
                 stopped = free_union(a, nl, tab, stage, used, lg, hcap, s_hist, &s_t, &s_nused,
                                      &s_nstage, &s_exit, &s_part, &s_item, &s_creq, s_T, s_vin,
-                                     can_stop, mode, first, b, l0, L, rv, my_bytes);
+                                     can_stop, mode, first, b, l0, L, rv, G, my_bytes);
             } else {
             // Flat mode, whole nodes of degree <= kFlatMax: every (list, 128-key
             // chunk) pair is one work item, warps take items in order, one per
@@ -1521,9 +1584,10 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
     const size_t dyn = levelU_smem(lg);
-    // free-running warps unless the stepped schedule is asked for (free is the
-    // faster one on every measured workload)
+    // free-running lane groups unless another schedule is asked for (grouped
+    // is the fastest, or within 2%, on every measured workload)
     void (*kern)(LevelArgs, int) = g.levelu_mode == KH_LEVELU_STEPPED ? k_levelU<false> : k_levelU<true>;
+    a.group_lists = g.levelu_mode == KH_LEVELU_FREE ? 0 : 1;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
     int per_sm = 0;

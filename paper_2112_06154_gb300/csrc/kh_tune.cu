@@ -116,9 +116,21 @@ __global__ void k_stride_sample(const int32_t* __restrict__ order, int64_t nsrc,
     if (blockIdx.x == 0 && threadIdx.x == 0) *count = (int)m;
 }
 
+// The sliced layout over `order` (nsrc sources, the first nbig of them too
+// large for the warp-per-source kernel): KH_VAR_SLICED_SMALL hands the rest
+// to that kernel.
+int run_sliced(Graph& g, const TuneChoice& c, int32_t* deg, int32_t* cnt, int jlo, int nj,
+               cudaStream_t s, const int32_t* order, int64_t nsrc, int64_t nbig) {
+    if (c.variant != KH_VAR_SLICED_SMALL)
+        return launch_hdeg2_slice(g, deg, cnt, jlo, nj, s, c.slices, c.threads, order, nsrc, true);
+    int rc = launch_hdeg2_slice(g, deg, cnt, jlo, nj, s, c.slices, c.threads, order, nbig, true);
+    if (rc) return rc;
+    return launch_hdeg2_small(g, deg, cnt, jlo, nj, s, order + nbig, nsrc - nbig);
+}
+
 // One candidate on the sample; returns its event time in ms (negative: failed).
 double time_candidate(Graph& g, const TuneChoice& c, const int32_t* sample, const int* d_count,
-                      int64_t m, int32_t* scratch, cudaStream_t s) {
+                      int64_t m, int32_t* scratch, cudaStream_t s, int64_t sample_big) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -132,8 +144,7 @@ double time_candidate(Graph& g, const TuneChoice& c, const int32_t* sample, cons
         if (c.variant == KH_VAR_CTA)
             rc = launch_hdeg(g, sample, d_count, 0, scratch, nullptr, 0, 0, s);
         else
-            rc = launch_hdeg2_slice(g, scratch, nullptr, 0, 0, s, c.slices, c.threads, sample, m,
-                                    true);
+            rc = run_sliced(g, c, scratch, nullptr, 0, 0, s, sample, m, sample_big);
         cudaEventRecord(e1, s);
         if (rc != KH_OK || cudaEventSynchronize(e1) != cudaSuccess) {
             cudaGetLastError();
@@ -173,7 +184,7 @@ int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out) {
     }
     const std::string key = shape_key(g, max_deg);
     TuneChoice c{};
-    if (table_find(key, &c) && (c.variant == KH_VAR_SLICED || cta_fits(g))) {
+    if (table_find(key, &c) && (c.variant != KH_VAR_CTA || cta_fits(g))) {
         g.tuned_hdeg2 = c;
         *out = c;
         return KH_OK;
@@ -185,11 +196,17 @@ int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out) {
     for (int si = 0; si < 4; ++si) {
         if (si > 0 && slist[si] == slist[si - 1]) continue;
         if (slist[si] > 64) continue;
-        for (int t : {256, 512, 1024}) cand.push_back({KH_VAR_SLICED, slist[si], t, 0.0});
+        for (int t : {256, 512, 1024}) {
+            cand.push_back({KH_VAR_SLICED, slist[si], t, 0.0});
+            cand.push_back({KH_VAR_SLICED_SMALL, slist[si], t, 0.0});
+        }
     }
     // sample: every stride-th source of the longest-first order
     const int64_t stride = g.nsrc2 > 65536 ? 32 : 1;
     const int64_t m = (g.nsrc2 + stride - 1) / stride;
+    // the stride sample keeps order2's order: its first sample_big sources are big
+    const int64_t big = hdeg2_small_split(g);
+    const int64_t sample_big = (big + stride - 1) / stride;
     int32_t* sample = g.listB;   // scratch (ensure_work holds n entries)
     int32_t* scratch = g.listA;
     int* d_count = &g.state->tune_count;
@@ -204,7 +221,7 @@ int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out) {
     best.ms = 1e30;
     for (TuneChoice& t : cand) {
         if (m == 0) break;
-        const double ms = time_candidate(g, t, sample, d_count, m, scratch, s);
+        const double ms = time_candidate(g, t, sample, d_count, m, scratch, s, sample_big);
         t.ms = ms;
         if (ms >= 0.0 && ms < best.ms) best = t;
     }
@@ -225,11 +242,10 @@ int run_hdeg_full(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStr
         TuneChoice c{};
         int rc = choose_hdeg2(g, s, &c);
         if (rc) return rc;
-        if (c.variant == KH_VAR_SLICED) {
+        if (c.variant == KH_VAR_SLICED || c.variant == KH_VAR_SLICED_SMALL) {
             rc = ensure_order2(g, s);
             if (rc) return rc;
-            return launch_hdeg2_slice(g, deg, cnt, jlo, nj, s, c.slices, c.threads, g.order2,
-                                      g.nsrc2, true);
+            return run_sliced(g, c, deg, cnt, jlo, nj, s, g.order2, g.nsrc2, hdeg2_small_split(g));
         }
     }
     return launch_hdeg(g, nullptr, nullptr, g.n, deg, cnt, jlo, nj, s);
@@ -248,7 +264,8 @@ extern "C" int kh_set_variant(kh_graph* G, int32_t op, int32_t variant, int32_t 
         return KH_OK;
     }
     if (op == KH_OP_LEVEL_UNION) {
-        if (variant != KH_VAR_AUTO && variant != KH_LEVELU_STEPPED && variant != KH_LEVELU_FREE)
+        if (variant != KH_VAR_AUTO && variant != KH_LEVELU_STEPPED && variant != KH_LEVELU_FREE &&
+            variant != KH_LEVELU_GROUPED)
             return kh::set_error(g.ctx, KH_EINVAL, "unknown union schedule %d", variant);
         g.levelu_mode = variant;
         return KH_OK;
@@ -265,13 +282,14 @@ extern "C" int kh_set_variant(kh_graph* G, int32_t op, int32_t variant, int32_t 
         g.force_hdeg2 = kh::TuneChoice{KH_VAR_CTA, 0, 256, 0.0};
         return KH_OK;
     }
-    if (variant != KH_VAR_SLICED) return kh::set_error(g.ctx, KH_EINVAL, "unknown variant %d", variant);
+    if (variant != KH_VAR_SLICED && variant != KH_VAR_SLICED_SMALL)
+        return kh::set_error(g.ctx, KH_EINVAL, "unknown variant %d", variant);
     if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
         return kh::set_error(g.ctx, KH_EINVAL, "threads must be 128, 256, 512 or 1024");
     if (slices < kh::hdeg2_min_slices(g.n) || slices > 1024 || (g.n > 0 && slices > g.n))
         return kh::set_error(g.ctx, KH_EINVAL, "slices must lie in [%d, min(1024, n)]",
                              kh::hdeg2_min_slices(g.n));
-    g.force_hdeg2 = kh::TuneChoice{KH_VAR_SLICED, slices, threads, 0.0};
+    g.force_hdeg2 = kh::TuneChoice{variant, slices, threads, 0.0};
     return KH_OK;
 }
 

@@ -33,12 +33,14 @@ KH_OP_HDEG2 = 0
 KH_VAR_AUTO = 0
 KH_VAR_CTA = 1
 KH_VAR_SLICED = 2
+KH_VAR_SLICED_SMALL = 3
 KH_OP_PEEL_COMPACT = 1
 KH_COMPACT_OFF = 1
 KH_COMPACT_ALWAYS = 2
 KH_OP_LEVEL_UNION = 2
 KH_LEVELU_STEPPED = 1
 KH_LEVELU_FREE = 2
+KH_LEVELU_GROUPED = 3
 PROF_NAMES = ["bfs", "level1", "levelU", "frontier", "peel"]
 
 _ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",

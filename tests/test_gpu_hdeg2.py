@@ -1,9 +1,11 @@
 """The two layouts of the whole-graph exact 2-degree pass and their autotuner.
 
 Every forced layout (one CTA per source; (source, slice) items with 1..64
-slices and 128..1024 threads per CTA) must give the oracle's exact 2-degrees
-(Sec. 2) and fixed-level counts element by element, on graphs with isolated
-nodes, ragged slice tails and hubs; the tuner's choice must be one of them.
+slices and 128..1024 threads per CTA; the same with the sources of small
+2-hop work on one warp each) must give the oracle's exact 2-degrees (Sec. 2)
+and fixed-level counts element by element, on graphs with isolated nodes,
+ragged slice tails, hubs, and 2-hop work on both sides of the warp kernel's
+limit (stars of 510 and 512 leaves); the tuner's choice must be one of them.
 """
 import os
 import subprocess
@@ -45,6 +47,10 @@ GRAPHS = {
     "cl20k": lambda: gg.chung_lu(20000, 20, 2.5, 1500, 1102),
     "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 7),
     "star": lambda: gg.star(300),
+    # every node's 2-hop work is the leaf count: 510 is the warp kernel's
+    # largest, 512 goes to the sliced kernel
+    "star510": lambda: gg.star(510),
+    "star512": lambda: gg.star(512),
     "path": lambda: gg.path(513),
 }
 
@@ -64,6 +70,7 @@ def test_every_layout_matches_the_oracle(ctx, name):
             if sl <= n:
                 for th in (128, 256, 1024):
                     layouts.append((K.KH_VAR_SLICED, sl, th))
+                    layouts.append((K.KH_VAR_SLICED_SMALL, sl, th))
         for var, sl, th in layouts:
             K.kh_set_variant(G, var, sl, th)
             assert (K.kh_hdegree_exact(G) == want).all(), (var, sl, th)
@@ -71,7 +78,7 @@ def test_every_layout_matches_the_oracle(ctx, name):
                 assert (K.kh_sampled_counts(G, 0, 10) == want_cnt).all(), (var, sl, th)
         K.kh_set_variant(G, K.KH_VAR_AUTO)
         var, sl, th, ms = K.kh_get_variant(G)
-        assert var in (K.KH_VAR_CTA, K.KH_VAR_SLICED) and ms >= 0.0
+        assert var in (K.KH_VAR_CTA, K.KH_VAR_SLICED, K.KH_VAR_SLICED_SMALL) and ms >= 0.0
         assert (K.kh_hdegree_exact(G) == want).all()
     finally:
         G.close()
@@ -101,7 +108,7 @@ def test_large_graph_uses_slices_only(ctx):
         with pytest.raises(K.KhError):
             K.kh_set_variant(G, K.KH_VAR_CTA)
         var, sl, th, _ = K.kh_get_variant(G)
-        assert var == K.KH_VAR_SLICED and sl >= 1
+        assert var in (K.KH_VAR_SLICED, K.KH_VAR_SLICED_SMALL) and sl >= 1
         deg = K.kh_hdegree_exact(G)
         assert (deg[:40000] == O.hdegree_exact(rp0, cl0, 2)).all()
         assert (deg[40000:] == 0).all()

@@ -1,5 +1,6 @@
-"""The two schedules of the level >= 2 union (Alg. 2 with Alg. 5's trim):
-barrier-separated steps and free-running warps.  Both must give the oracle's
+"""The three schedules of the level >= 2 union (Alg. 2 with Alg. 5's trim):
+barrier-separated steps, free-running warps, and free-running lane groups
+(fewer lanes per list as the lists outnumber the warps).  All must give the oracle's
 estimates (levels and |B|) and sampled cores bit for bit, including split hubs,
 small M (many trims and compactions) and refines that stop early."""
 import numpy as np
@@ -17,7 +18,8 @@ GRAPHS = {
     "hubs": lambda: gg.with_hubs(12000, (9000, 6000, 4500), 77),
     "rmat12": lambda: gg.rmat(12, 16, 0.57, 0.19, 0.19, 5),
 }
-MODES = {"stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE}
+MODES = {"stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE,
+         "grouped": K.KH_LEVELU_GROUPED}
 
 
 @pytest.fixture(scope="module")
