@@ -173,6 +173,9 @@ def parse():
     p.add_argument("--variant", default=None,
                    help="--op hdeg2/counts2 only: force the 2-degree layout: 'cta', 'sliced,S,T' or "
                         "'small,S,T' (sliced, small balls one warp each)")
+    p.add_argument("--sweep", default=None,
+                   help="--op hdeg2 only: 'off', or a work bin b: sources of 2-hop work >= 2^b - 1 "
+                        "go to the bit-parallel sweeps (default: the tuner's choice)")
     p.add_argument("--union", choices=["auto", "stepped", "free", "grouped"], default="auto",
                    help="schedule of the level-union kernel (kh_set_variant KH_OP_LEVEL_UNION)")
     p.add_argument("--prof", action="store_true",
@@ -259,9 +262,11 @@ def load_peak():
         return 6800.0, "fallback"
 
 
-def profile_traffic(workload, kind_name):
+def profile_traffic(workload, kind_name, alg_bytes_per_launch):
     """DRAM bytes per launch of a kernel class on a workload, from the committed
-    ncu summary (None when the class is not listed there)."""
+    ncu summaries (None when the class is not listed).  A line gives either the
+    bytes per launch, or 'ratio R': DRAM bytes per algorithmic byte measured on
+    windows of launches, applied to this run's algorithmic bytes per launch."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     try:
         with open(path) as f:
@@ -270,6 +275,8 @@ def profile_traffic(workload, kind_name):
                 if line.startswith("#") or len(parts) < 3:
                     continue
                 if parts[0] == workload and parts[1] == kind_name:
+                    if parts[2] == "ratio" and len(parts) >= 4:
+                        return float(parts[3]) * alg_bytes_per_launch
                     return float(parts[2])
     except OSError:
         pass
@@ -391,7 +398,7 @@ def run_ours(args):
     d = prof[dom]
     peak, peak_src = load_peak()
     achieved = (d["alg_bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
-    traffic = profile_traffic(wl.name, dom)
+    traffic = profile_traffic(wl.name, dom, d["alg_bytes"] / max(d["launches"], 1))
     roofline = {"bound": "hbm", "kernel": CLASS_KERNELS.get(dom, dom), "class": dom,
                 "achieved": round(achieved, 2), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -513,6 +520,12 @@ def run_op(args):
         else:
             var = K.KH_VAR_SLICED_SMALL if f[0] == "small" else K.KH_VAR_SLICED
             K.kh_set_variant(G, var, int(f[1]), int(f[2]))
+    if args.sweep == "off":
+        K.kh_set_variant(G, K.KH_SWEEP_OFF, op=K.KH_OP_HDEG2_SWEEP)
+    elif args.sweep is not None:
+        K.kh_set_variant(G, K.KH_SWEEP_FROM, int(args.sweep), 0, op=K.KH_OP_HDEG2_SWEEP)
+    if op in ("hdeg", "counts") and h == 2:
+        K.kh_get_variant(G)  # the tuner (if it runs) stays out of the timed call
     if args.prof:
         K.kh_prof_enable(G, True)
     t0 = time.perf_counter()
@@ -532,6 +545,7 @@ def run_op(args):
                     "per_launch_ms": K.kh_prof_trace(G, kind).tolist()[:8]}
     if op in ("hdeg", "counts") and h == 2:
         info["variant"] = K.kh_get_variant(G)
+        info["sweep"] = K.kh_get_variant(G, op=K.KH_OP_HDEG2_SWEEP)[:2]
     print(json.dumps(info), flush=True)
     G.close()
     ctx.close()

@@ -228,6 +228,11 @@ int kh_prof_read(kh_graph *g, int32_t kind, double *ms, int64_t *launches, doubl
  * the number recorded.  KH_EINVAL for a NULL count, a negative cap, or
  * cap > 0 with a NULL ms. */
 int kh_prof_trace(kh_graph *g, int32_t kind, float *ms, int64_t cap, int64_t *count);
+/* The algorithmic bytes of the same brackets, in the same order (the class's
+ * device counter copied before and after each bracket; UINT64_MAX where the
+ * copy was not made: more than 2^20 brackets between two reads, or no device
+ * memory for the copies).  Same argument rules as kh_prof_trace. */
+int kh_prof_trace_bytes(kh_graph *g, int32_t kind, uint64_t *bytes, int64_t cap, int64_t *count);
 
 /* Number of CUDA kernels the library has launched for this graph since it was
  * loaded (kernels inside a replayed CUDA graph count one each per replay).
@@ -305,6 +310,17 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
 #define KH_LEVELU_STEPPED 1
 #define KH_LEVELU_FREE 2
 #define KH_LEVELU_GROUPED 3
+/* KH_OP_HDEG2_SWEEP: the whole-graph exact 2-degrees (kh_hdegree_exact at
+ * h = 2 with a sliced layout) may hand the sources of largest 2-hop work
+ * (sum of their neighbours' degrees) to bit-parallel sweeps: one pass over
+ * every row per batch of 128 sources, with 128-bit source masks per node.
+ * KH_VAR_AUTO: the tuner decides the threshold; KH_SWEEP_OFF: never;
+ * KH_SWEEP_FROM: the sources of work >= 2^slices - 1 (slices in [1, 48)).
+ * kh_get_variant with this op reports KH_SWEEP_OFF or KH_SWEEP_FROM and the
+ * bin in *slices.  The degrees are the same every way. */
+#define KH_OP_HDEG2_SWEEP 3
+#define KH_SWEEP_OFF 1
+#define KH_SWEEP_FROM 2
 int kh_set_variant(kh_graph *g, int32_t op, int32_t variant, int32_t slices, int32_t threads);
 int kh_get_variant(kh_graph *g, int32_t op, int32_t *variant, int32_t *slices, int32_t *threads,
                    double *tuned_ms);

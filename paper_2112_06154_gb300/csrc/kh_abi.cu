@@ -111,18 +111,37 @@ void prof_begin(Graph& g, int kind, cudaStream_t s) {
     if (!g.prof_on) return;
     cudaEvent_t e = pool_event(g);
     if (!e) return;
+    int64_t si = -1;
+    if (g.prof_snap && g.prof_nsnap + 2 <= kProfSnapCap &&
+        cudaMemcpyAsync(g.prof_snap + g.prof_nsnap, &g.state->bytes[kind], sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, s) == cudaSuccess) {
+        si = g.prof_nsnap;
+        g.prof_nsnap += 2;
+    }
     cudaEventRecord(e, s);
     g.prof_kind->push_back(kind);
     g.prof_ev->push_back(e);
+    g.prof_snapi->push_back(si);
 }
 
 void prof_end(Graph& g, int kind, cudaStream_t s) {
     if (!g.prof_on) return;
-    (void)kind;
+    if (g.prof_ev->size() != 2 * g.prof_kind->size() - 1) return;  // its begin was not recorded
     cudaEvent_t e = pool_event(g);
-    if (!e) return;
+    if (!e) {
+        // drop the open bracket
+        g.ev_pool->push_back(g.prof_ev->back());
+        g.prof_ev->pop_back();
+        g.prof_kind->pop_back();
+        g.prof_snapi->pop_back();
+        return;
+    }
     cudaEventRecord(e, s);
     g.prof_ev->push_back(e);
+    const int64_t si = g.prof_snapi->back();
+    if (si >= 0 && cudaMemcpyAsync(g.prof_snap + si + 1, &g.state->bytes[kind], sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        g.prof_snapi->back() = -1;
 }
 
 // Fold recorded event pairs into the per-kind totals (synchronizes the stream).
@@ -130,6 +149,10 @@ static int prof_collect(Graph& g) {
     if (!g.prof_ev || g.prof_ev->empty()) return KH_OK;
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(g.ctx->stream));
     const size_t pairs = g.prof_kind->size();
+    std::vector<unsigned long long> snap((size_t)g.prof_nsnap);
+    if (g.prof_nsnap > 0)
+        KH_CUDA_TRY(g.ctx, cudaMemcpy(snap.data(), g.prof_snap, sizeof(unsigned long long) * snap.size(),
+                                      cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < pairs && 2 * i + 1 < g.prof_ev->size(); ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, (*g.prof_ev)[2 * i], (*g.prof_ev)[2 * i + 1]) == cudaSuccess) {
@@ -138,6 +161,10 @@ static int prof_collect(Graph& g) {
             g.prof_launches[k] += 1;
             if (!g.prof_trace[k]) g.prof_trace[k] = new std::vector<float>();
             g.prof_trace[k]->push_back(ms);
+            // bytes of the bracket (~0: not recorded)
+            const int64_t si = (*g.prof_snapi)[i];
+            if (!g.prof_btrace[k]) g.prof_btrace[k] = new std::vector<unsigned long long>();
+            g.prof_btrace[k]->push_back(si >= 0 ? snap[(size_t)si + 1] - snap[(size_t)si] : ~0ull);
         } else {
             cudaGetLastError();
         }
@@ -145,6 +172,8 @@ static int prof_collect(Graph& g) {
     for (cudaEvent_t e : *g.prof_ev) g.ev_pool->push_back(e);
     g.prof_ev->clear();
     g.prof_kind->clear();
+    g.prof_snapi->clear();
+    g.prof_nsnap = 0;
     return KH_OK;
 }
 
@@ -257,6 +286,14 @@ static void free_graph_arrays(Graph& g) {
     dfree(&g.degX);
     dfree(&g.lb64);
     dfree(&g.order2);
+    dfree(&g.sw_m1);
+    dfree(&g.sw_filter);
+    dfree(&g.sw_hpos);
+    dfree(&g.sw_piece_h);
+    dfree(&g.sw_piece_off);
+    dfree(&g.sw_hnode);
+    dfree(&g.sw_bh);
+    dfree(&g.sw_cnt);
     dfree(&g.bestnb);
     for (int b = 0; b < 2; ++b) {
         dfree(&g.cp_row[b]);
@@ -289,9 +326,15 @@ static void free_graph_arrays(Graph& g) {
     }
     delete g.prof_kind;
     g.prof_kind = nullptr;
+    delete g.prof_snapi;
+    g.prof_snapi = nullptr;
+    if (g.prof_snap) cudaFree(g.prof_snap);
+    g.prof_snap = nullptr;
     for (int k = 0; k < kProfKinds; ++k) {
         delete g.prof_trace[k];
         g.prof_trace[k] = nullptr;
+        delete g.prof_btrace[k];
+        g.prof_btrace[k] = nullptr;
     }
 }
 
@@ -854,14 +897,25 @@ int kh_prof_enable(kh_graph* G, int32_t on) {
     KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(g.ctx->stream));
     if (!g.prof_ev) g.prof_ev = new std::vector<cudaEvent_t>();
     if (!g.prof_kind) g.prof_kind = new std::vector<int>();
+    if (!g.prof_snapi) g.prof_snapi = new std::vector<int64_t>();
     if (!g.ev_pool) g.ev_pool = new std::vector<cudaEvent_t>();
     for (cudaEvent_t e : *g.prof_ev) g.ev_pool->push_back(e);
     g.prof_ev->clear();
     g.prof_kind->clear();
+    g.prof_snapi->clear();
+    g.prof_nsnap = 0;
+    // the byte snapshots are optional: without their buffer the byte trace reads ~0
+    if (on && !g.prof_snap &&
+        cudaMalloc((void**)&g.prof_snap, sizeof(unsigned long long) * (size_t)kh::kProfSnapCap) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        g.prof_snap = nullptr;
+    }
     for (int k = 0; k < kh::kProfKinds; ++k) {
         g.prof_ms[k] = 0.0;
         g.prof_launches[k] = 0;
         if (g.prof_trace[k]) g.prof_trace[k]->clear();
+        if (g.prof_btrace[k]) g.prof_btrace[k]->clear();
     }
     KH_CUDA_TRY(g.ctx, cudaMemset(g.state->bytes, 0, sizeof(g.state->bytes)));
     g.prof_on = on != 0;
@@ -893,6 +947,20 @@ int kh_prof_trace(kh_graph* G, int32_t kind, float* ms, int64_t cap, int64_t* co
     const std::vector<float>* t = g.prof_trace[kind];
     const int64_t total = t ? (int64_t)t->size() : 0;
     for (int64_t i = 0; i < total && i < cap; ++i) ms[i] = (*t)[(size_t)i];
+    *count = total;
+    return KH_OK;
+}
+
+int kh_prof_trace_bytes(kh_graph* G, int32_t kind, uint64_t* bytes, int64_t cap, int64_t* count) {
+    if (!G || !count || cap < 0 || (cap > 0 && !bytes)) return KH_EINVAL;
+    Graph& g = G->g;
+    if (kind < 0 || kind >= kh::kProfKinds) return kh::set_error(g.ctx, KH_EINVAL, "bad profiling kind");
+    cudaSetDevice(g.ctx->device);
+    int rc = kh::prof_collect(g);
+    if (rc) return rc;
+    const std::vector<unsigned long long>* t = g.prof_btrace[kind];
+    const int64_t total = t ? (int64_t)t->size() : 0;
+    for (int64_t i = 0; i < total && i < cap; ++i) bytes[i] = (uint64_t)(*t)[(size_t)i];
     *count = total;
     return KH_OK;
 }

@@ -18,6 +18,8 @@
 //
 // The bitmap is cleared between items through the list of words the item set
 // first (when it fits), otherwise with vector stores over the whole slice.
+#include <vector>
+
 #include "kh_internal.cuh"
 
 namespace kh {
@@ -28,7 +30,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kMaxHeavy2 = 128;      // rows expanded by the whole CTA per item
 constexpr int kHeavyRow2 = 512;      // a row part this long goes to the whole CTA
 constexpr int kTouchCap = 4096;      // words cleared one by one (else full clear)
-constexpr int kOrderBins = 48;       // log2 bins of the 2-hop work
+constexpr int kOrderBins = kOrderBinsMax;  // log2 bins of the 2-hop work
 
 struct Slice2Args {
     const int64_t* rowptr;
@@ -366,6 +368,192 @@ __global__ void k_init2(const int64_t* __restrict__ rowptr, const uint8_t* __res
     }
 }
 
+// ---- bit-parallel sweeps for the sources of largest 2-hop work ----
+// For a batch of up to 128 sources s_j, m1[u] holds bit j when u is a
+// neighbour of s_j.  A node x lies in N(s_j; 2) exactly when bit j is set in
+// m1[x] | OR_{u in A(x)} m1[u] (x = s_j itself through any neighbour u, as s_j
+// is in A(u)).  One sweep over all rows thus gives the 2-balls of 128 sources:
+// it reads each row once (2m column ids and 2m 16-byte gathers from m1, which
+// stays in L2), where the per-source union reads sum_{w in A(s_j)} deg(w)
+// entries for each source.  It pays off for sources whose 2-hop work exceeds
+// about one pass over the graph per batch.  A filter of one bit per 4 nodes
+// (some of them has source bits), held in shared memory by the count kernel,
+// skips the gathers of entries that cannot contribute: for batches of
+// mid-size sources half of all entries or more.
+constexpr int kSweepSrc = 128;
+constexpr int kSweepHead = 512;    // row entries the count kernel reads itself
+constexpr int kSweepPiece = 2048;  // entries per tail piece of a longer row
+constexpr int kSweepPlanes = 8;    // carry-save counter planes: 255 additions between flushes
+
+// Set (clear = 0) or zero (clear = 1) the batch's source bits on the
+// neighbours of its sources; the setting pass also counts each source's
+// algorithmic bytes (those of one 2-hop search).
+__global__ void k_sweep_scatter(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ src, int nb, uint32_t* __restrict__ m1,
+                                uint32_t* __restrict__ filter, int clear, unsigned long long* bytes) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long my = 0;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nw) {
+        const int v = src[j];
+        const int64_t b = rowptr[v], e = rowptr[v + 1];
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t u = __ldg(col + k);
+            if (clear) {
+                reinterpret_cast<uint4*>(m1)[u] = make_uint4(0u, 0u, 0u, 0u);
+                filter[u >> 7] = 0u;
+            } else {
+                atomicOr(m1 + 4 * (size_t)u + (j >> 5), 1u << (j & 31));
+                atomicOr(filter + (u >> 7), 1u << ((u >> 2) & 31));
+                my += 8ull + 4ull * (unsigned long long)(rowptr[u + 1] - rowptr[u]);
+            }
+        }
+        if (!clear && lane == 0) my += 8ull + 4ull * (unsigned long long)(e - b) + 4ull;
+    }
+    if (clear) return;
+    for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(kFull, my, off);
+    if (lane == 0 && my) atomicAdd(bytes, my);
+}
+
+__device__ __forceinline__ void or4(uint4& a, const uint4 b) {
+    a.x |= b.x;
+    a.y |= b.y;
+    a.z |= b.z;
+    a.w |= b.w;
+}
+
+// Rows longer than kSweepHead: the OR of m1 over each tail piece of
+// kSweepPiece entries, into that row's partial word bh (zeroed per sweep).
+__global__ void k_sweep_tails(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const int32_t* __restrict__ hnode, const int32_t* __restrict__ piece_h,
+                              const int32_t* __restrict__ piece_off, int64_t npieces,
+                              const uint4* __restrict__ m1, const uint32_t* __restrict__ filter,
+                              uint32_t* __restrict__ bh) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < npieces; p += nw) {
+        const int h = piece_h[p];
+        const int x = hnode[h];
+        const int64_t b = rowptr[x] + piece_off[p];
+        const int64_t re = rowptr[x + 1];
+        const int64_t e = b + kSweepPiece < re ? b + kSweepPiece : re;
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t k = b + lane; k < e; k += 32) {
+            const int32_t u = __ldg(col + k);
+            if ((__ldg(filter + (u >> 7)) >> ((u >> 2) & 31)) & 1u) or4(acc, __ldg(m1 + u));
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x |= __shfl_xor_sync(kFull, acc.x, off);
+            acc.y |= __shfl_xor_sync(kFull, acc.y, off);
+            acc.z |= __shfl_xor_sync(kFull, acc.z, off);
+            acc.w |= __shfl_xor_sync(kFull, acc.w, off);
+        }
+        if (lane < 4) {
+            const uint32_t w = lane == 0 ? acc.x : lane == 1 ? acc.y : lane == 2 ? acc.z : acc.w;
+            if (w) atomicOr(bh + 4 * (size_t)h + lane, w);
+        }
+    }
+}
+
+// Add the counts held in carry-save planes (bit `bit` of plane p is worth
+// 2^p) to the block's per-source counters; lane gl of a group owns bits
+// [16 gl, 16 gl + 16) of the ball word.
+__device__ __forceinline__ void sweep_flush(uint32_t (&c)[kSweepPlanes], unsigned int* s_cnt, int gl) {
+#pragma unroll
+    for (int bit = 0; bit < 16; ++bit) {
+        unsigned int v = 0;
+#pragma unroll
+        for (int p = 0; p < kSweepPlanes; ++p) v |= ((c[p] >> bit) & 1u) << p;
+        if (v) atomicAdd(&s_cnt[16 * gl + bit], v);
+    }
+#pragma unroll
+    for (int p = 0; p < kSweepPlanes; ++p) c[p] = 0u;
+}
+
+// Ball words of every node (groups of 8 lanes per node, four nodes per warp
+// step; a row's first kSweepHead entries here, the rest from bh) and the
+// number of nodes in each source's ball (per-lane carry-save counters of 16
+// source bits, flushed every 255 nodes).  With use_filter the filter's
+// fwords words are first copied to shared memory.
+__global__ void __launch_bounds__(1024) k_sweep_count(const int64_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col, int64_t n,
+                                                      const uint4* __restrict__ m1,
+                                                      const uint32_t* __restrict__ filter,
+                                                      int use_filter, int fwords,
+                                                      const int32_t* __restrict__ hpos,
+                                                      const uint4* __restrict__ bh,
+                                                      unsigned int* __restrict__ cnt) {
+    extern __shared__ __align__(16) uint32_t s_filter[];
+    __shared__ unsigned int s_cnt[kSweepSrc];
+    for (int i = threadIdx.x; i < kSweepSrc; i += blockDim.x) s_cnt[i] = 0u;
+    if (use_filter) {
+        const uint4* f4 = reinterpret_cast<const uint4*>(filter);
+        uint4* s4 = reinterpret_cast<uint4*>(s_filter);
+        for (int i = threadIdx.x; i < (fwords >> 2); i += blockDim.x) s4[i] = f4[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c[kSweepPlanes];
+#pragma unroll
+    for (int p = 0; p < kSweepPlanes; ++p) c[p] = 0u;
+    int adds = 0;
+    // the loop bound is the same for the whole warp (the shuffles need every lane)
+    for (int64_t x0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; x0 < n; x0 += nw * 4) {
+        const int64_t x = x0 + g;
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+        if (x < n) {
+            const int64_t b = rowptr[x], e = rowptr[x + 1];
+            if (e > b) {
+                if (gl == 0) acc = m1[x];
+                const int64_t he = e - b > kSweepHead ? b + kSweepHead : e;
+                if (use_filter) {
+                    for (int64_t k = b + gl; k < he; k += 8) {
+                        const int32_t u = __ldg(col + k);
+                        if ((s_filter[u >> 7] >> ((u >> 2) & 31)) & 1u) or4(acc, __ldg(m1 + u));
+                    }
+                } else {
+                    for (int64_t k = b + gl; k < he; k += 8) or4(acc, __ldg(m1 + __ldg(col + k)));
+                }
+                if (gl == 1 && e - b > kSweepHead) or4(acc, bh[hpos[x]]);
+            }
+        }
+        for (int off = 1; off < 8; off <<= 1) {
+            acc.x |= __shfl_xor_sync(kFull, acc.x, off);
+            acc.y |= __shfl_xor_sync(kFull, acc.y, off);
+            acc.z |= __shfl_xor_sync(kFull, acc.z, off);
+            acc.w |= __shfl_xor_sync(kFull, acc.w, off);
+        }
+        const int wi = gl >> 1;
+        const uint32_t word = wi == 0 ? acc.x : wi == 1 ? acc.y : wi == 2 ? acc.z : acc.w;
+        uint32_t carry = (gl & 1) ? (word >> 16) : (word & 0xffffu);
+#pragma unroll
+        for (int p = 0; p < kSweepPlanes; ++p) {
+            const uint32_t t = c[p] & carry;
+            c[p] ^= carry;
+            carry = t;
+        }
+        if (++adds == (1 << kSweepPlanes) - 1) {
+            sweep_flush(c, s_cnt, gl);
+            adds = 0;
+        }
+    }
+    sweep_flush(c, s_cnt, gl);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSweepSrc; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(cnt + i, s_cnt[i]);
+}
+
+// deg_2 of the batch's sources (the ball holds the source itself); the
+// counters are zeroed for the next sweep.
+__global__ void k_sweep_finish(const int32_t* __restrict__ src, int nb, unsigned int* __restrict__ cnt,
+                               int32_t* __restrict__ deg, unsigned long long* updates) {
+    const int j = threadIdx.x;
+    if (j < nb) deg[src[j]] = (int32_t)cnt[j] - 1;
+    if (j < kSweepSrc) cnt[j] = 0u;
+    if (j == 0) atomicAdd(updates, (unsigned long long)nb);
+}
+
 }  // namespace
 
 size_t hdeg2_smem(int64_t width) { return (size_t)(width / 8) + (size_t)kTouchCap * 4; }
@@ -455,6 +643,115 @@ int launch_hdeg2_small(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cu
                                                    nj, &g.state->updates, &g.state->bytes[kProfBfs]);
     count_launch(g, 1);
     prof_end(g, kProfBfs, s);
+    return KH_OK;
+}
+
+int64_t hdeg2_sources_from_bin(const Graph& g, int bin) {
+    int64_t c = 0;
+    for (int b = bin < 0 ? 0 : bin; b < kOrderBins; ++b) c += g.order2_hist[b];
+    return c;
+}
+
+// The sweep's per-graph arrays: m1 (zeroed), the rows longer than kSweepHead
+// and their tail pieces, the counters.
+static int ensure_sweep(Graph& g, cudaStream_t s) {
+    if (g.sw_m1) return KH_OK;
+    const size_t n = (size_t)(g.n > 0 ? g.n : 1);
+    std::vector<int64_t> rp((size_t)g.n + 1);
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(rp.data(), g.rowptr, sizeof(int64_t) * rp.size(),
+                                       cudaMemcpyDeviceToHost, s));
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));
+    std::vector<int32_t> hpos(n, -1), hnode, piece_h, piece_off;
+    for (int64_t x = 0; x < g.n; ++x) {
+        const int64_t d = rp[(size_t)x + 1] - rp[(size_t)x];
+        if (d <= kSweepHead) continue;
+        const int h = (int)hnode.size();
+        hpos[(size_t)x] = h;
+        hnode.push_back((int32_t)x);
+        for (int64_t off = kSweepHead; off < d; off += kSweepPiece) {
+            piece_h.push_back(h);
+            piece_off.push_back((int32_t)off);
+        }
+    }
+    const size_t nh = hnode.size() > 0 ? hnode.size() : 1;
+    const size_t np = piece_h.size() > 0 ? piece_h.size() : 1;
+    int rc;
+    const size_t fw = ((n + 127) / 128 + 3) & ~(size_t)3;  // filter words, a multiple of 4
+    if ((rc = alloc_bytes(g.ctx, (void**)&g.sw_m1, 16 * n, "sweep source bits")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_filter, 4 * fw, "sweep filter")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_hpos, 4 * n, "sweep row index")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_hnode, 4 * nh, "sweep long rows")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_bh, 16 * nh, "sweep tail words")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_piece_h, 4 * np, "sweep pieces")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_piece_off, 4 * np, "sweep pieces")) ||
+        (rc = alloc_bytes(g.ctx, (void**)&g.sw_cnt, 4 * kSweepSrc, "sweep counts"))) {
+        cudaFree(g.sw_m1); cudaFree(g.sw_filter); cudaFree(g.sw_hpos); cudaFree(g.sw_hnode); cudaFree(g.sw_bh);
+        cudaFree(g.sw_piece_h); cudaFree(g.sw_piece_off); cudaFree(g.sw_cnt);
+        g.sw_m1 = nullptr; g.sw_filter = nullptr; g.sw_hpos = nullptr; g.sw_hnode = nullptr; g.sw_bh = nullptr;
+        g.sw_piece_h = nullptr; g.sw_piece_off = nullptr; g.sw_cnt = nullptr;
+        return rc;
+    }
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.sw_m1, 0, 16 * n, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.sw_filter, 0, 4 * fw, s));
+    KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.sw_cnt, 0, 4 * kSweepSrc, s));
+    KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.sw_hpos, hpos.data(), 4 * n, cudaMemcpyHostToDevice, s));
+    if (!hnode.empty()) {
+        KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.sw_hnode, hnode.data(), 4 * hnode.size(),
+                                           cudaMemcpyHostToDevice, s));
+        KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.sw_piece_h, piece_h.data(), 4 * piece_h.size(),
+                                           cudaMemcpyHostToDevice, s));
+        KH_CUDA_TRY(g.ctx, cudaMemcpyAsync(g.sw_piece_off, piece_off.data(), 4 * piece_off.size(),
+                                           cudaMemcpyHostToDevice, s));
+    }
+    KH_CUDA_TRY(g.ctx, cudaStreamSynchronize(s));  // host vectors go out of scope
+    g.sw_nheavy = (int64_t)hnode.size();
+    g.sw_npieces = (int64_t)piece_h.size();
+    return KH_OK;
+}
+
+int run_sweeps(Graph& g, int32_t* deg, const int32_t* src, int64_t count, cudaStream_t s) {
+    if (count <= 0) return KH_OK;
+    int rc = ensure_sweep(g, s);
+    if (rc) return rc;
+    // the filter in shared memory while it fits (n up to 7.2M nodes)
+    const size_t n1 = (size_t)(g.n > 0 ? g.n : 1);
+    const int fwords = (int)(((n1 + 127) / 128 + 3) & ~(size_t)3);
+    const size_t fsm = (size_t)fwords * 4;
+    const int use_filter = fsm <= (size_t)kSmem2Max ? 1 : 0;
+    const size_t dyn = use_filter ? fsm : 0;
+    KH_CUDA_TRY(g.ctx, cudaFuncSetAttribute(k_sweep_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(dyn > 0 ? dyn : 16)));
+    int per_sm = 0;
+    KH_CUDA_TRY(g.ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_count, 1024, dyn));
+    if (per_sm < 1) return set_error(g.ctx, KH_EINVAL, "sweep kernel does not fit on an SM");
+    const int cgrid = g.ctx->sm_count * per_sm;
+    int64_t tgrid = (g.sw_npieces + 7) / 8;
+    if (tgrid > (int64_t)g.ctx->sm_count * 8) tgrid = (int64_t)g.ctx->sm_count * 8;
+    if (tgrid < 1) tgrid = 1;
+    prof_begin(g, kProfBfs, s);
+    int64_t sweeps = 0;
+    for (int64_t b0 = 0; b0 < count; b0 += kSweepSrc, ++sweeps) {
+        const int nb = (int)(count - b0 < kSweepSrc ? count - b0 : kSweepSrc);
+        const int sgrid = (nb + 7) / 8;
+        k_sweep_scatter<<<sgrid, 256, 0, s>>>(g.rowptr, g.col, src + b0, nb, g.sw_m1, g.sw_filter, 0,
+                                              &g.state->bytes[kProfBfs]);
+        if (g.sw_npieces > 0) {
+            KH_CUDA_TRY(g.ctx, cudaMemsetAsync(g.sw_bh, 0, 16 * (size_t)g.sw_nheavy, s));
+            k_sweep_tails<<<(int)tgrid, 256, 0, s>>>(g.rowptr, g.col, g.sw_hnode, g.sw_piece_h,
+                                                     g.sw_piece_off, g.sw_npieces,
+                                                     reinterpret_cast<const uint4*>(g.sw_m1), g.sw_filter,
+                                                     g.sw_bh);
+        }
+        k_sweep_count<<<cgrid, 1024, dyn, s>>>(g.rowptr, g.col, g.n, reinterpret_cast<const uint4*>(g.sw_m1),
+                                               g.sw_filter, use_filter, fwords, g.sw_hpos,
+                                               reinterpret_cast<const uint4*>(g.sw_bh), g.sw_cnt);
+        k_sweep_finish<<<1, kSweepSrc, 0, s>>>(src + b0, nb, g.sw_cnt, deg, &g.state->updates);
+        k_sweep_scatter<<<sgrid, 256, 0, s>>>(g.rowptr, g.col, src + b0, nb, g.sw_m1, g.sw_filter, 1,
+                                              nullptr);
+    }
+    count_launch(g, sweeps * (g.sw_npieces > 0 ? 5 : 4));
+    prof_end(g, kProfBfs, s);
+    KH_CUDA_TRY(g.ctx, cudaGetLastError());
     return KH_OK;
 }
 

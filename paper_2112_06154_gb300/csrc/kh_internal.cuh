@@ -46,6 +46,9 @@ constexpr int kErrProbe = 2;   // hash probe limit reached
 constexpr int kErrList = 4;    // list larger than its slot
 constexpr int kErrGraph = 8;   // CSR validation failure
 constexpr int kErrLoop = 16;   // a work loop ran past its iteration bound
+constexpr int64_t kProfSnapCap = 1 << 21;  // byte snapshots kept between two reads
+constexpr int kOrderBinsMax = 48;  // log2 bins of a source's 2-hop work (order2)
+constexpr int kSweepMinBin = 16;   // smallest work bin the tuner offers to the sweeps
 
 // Kernel classes for the profiling counters (kh_prof_read kinds).
 constexpr int kProfBfs = 0;       // exact h-degree / fixed-level count BFS
@@ -119,6 +122,7 @@ struct TuneChoice {
     int slices;
     int threads;
     double ms;
+    int sweep_bin;  // sources with 2-hop work >= 2^sweep_bin go to the bit-parallel sweeps (0: none)
 };
 
 // NVTX range for profilers and tracers (a no-op unless a tool is attached).
@@ -166,6 +170,10 @@ size_t hdeg2_smem(int64_t width);
 // sources of order2 whose 2-hop work is too large for the warp-per-source
 // kernel (they come first in order2), and that kernel for the rest
 int64_t hdeg2_small_split(const Graph& g);
+// sources of order2 whose 2-hop work is at least 2^bin (they come first)
+int64_t hdeg2_sources_from_bin(const Graph& g, int bin);
+// exact 2-degrees of `count` sources by bit-parallel sweeps of 128 sources
+int run_sweeps(Graph& g, int32_t* deg, const int32_t* src, int64_t count, cudaStream_t s);
 int launch_hdeg2_small(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStream_t s,
                        const int32_t* order, int64_t count);
 // kh_tune.cu: the layout of the 2-degree pass for this graph (tuned once), and
@@ -308,6 +316,12 @@ struct Graph {
     double prof_ms[kProfKinds];
     int64_t prof_launches[kProfKinds];
     std::vector<float>* prof_trace[kProfKinds];  // per-bracket ms, in launch order
+    // per-bracket algorithmic bytes: the class counter copied before and after
+    // each bracket into prof_snap (device; prof_snapi: first slot or -1)
+    unsigned long long* prof_snap;
+    int64_t prof_nsnap;
+    std::vector<int64_t>* prof_snapi;
+    std::vector<unsigned long long>* prof_btrace[kProfKinds];
     // cached CUDA graph of a batch of peeling rounds
     cudaGraphExec_t round_exec;
     int round_exec_key[10];
@@ -349,6 +363,19 @@ struct Graph {
     int32_t *order2;
     int64_t nsrc2;
     int64_t order2_hist[48];  // sources per log2 bin of 2-hop work (order2 is by descending bin)
+    // bit-parallel 2-degree sweeps: source bits of the batch per node (128 per
+    // node), node index among the rows longer than the sweep's head (or -1),
+    // those rows' tail pieces and their partial ORs, per-bit ball counts
+    uint32_t* sw_m1;
+    uint32_t* sw_filter;      // one bit per 4 nodes: some of them has source bits in m1
+    int32_t* sw_hpos;
+    int32_t* sw_piece_h;
+    int32_t* sw_piece_off;
+    int32_t* sw_hnode;
+    uint32_t* sw_bh;
+    unsigned int* sw_cnt;
+    int64_t sw_nheavy, sw_npieces;
+    int sw_force;             // forced sweep threshold bin (0: tuner; -1: no sweeps)
     // each node's neighbour of largest degree (-1: none), for cheap stale bounds
     int32_t *bestnb;
     // the 2-degree pass layout: forced by kh_set_variant, or chosen by the tuner

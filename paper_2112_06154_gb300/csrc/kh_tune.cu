@@ -37,6 +37,7 @@ struct TableRow {
     std::string key;
     int variant, slices, threads;
     double ms;
+    int sweep_bin;
 };
 
 std::mutex g_table_mu;
@@ -63,14 +64,15 @@ void load_table_locked() {
     if (!f) return;
     char line[512];
     while (fgets(line, sizeof(line), f)) {
-        // key words ... | variant slices threads ms
+        // key words ... | variant slices threads ms [sweep_bin]
         char* bar = strchr(line, '|');
         if (!bar || line[0] == '#') continue;
         *bar = 0;
         TableRow r;
         r.key = line;
+        r.sweep_bin = 0;
         while (!r.key.empty() && r.key.back() == ' ') r.key.pop_back();
-        if (sscanf(bar + 1, "%d %d %d %lf", &r.variant, &r.slices, &r.threads, &r.ms) == 4)
+        if (sscanf(bar + 1, "%d %d %d %lf %d", &r.variant, &r.slices, &r.threads, &r.ms, &r.sweep_bin) >= 4)
             g_table->push_back(r);
     }
     fclose(f);
@@ -85,6 +87,7 @@ bool table_find(const std::string& key, TuneChoice* out) {
             out->slices = it->slices;
             out->threads = it->threads;
             out->ms = it->ms;
+            out->sweep_bin = it->sweep_bin;
             return true;
         }
     return false;
@@ -93,12 +96,12 @@ bool table_find(const std::string& key, TuneChoice* out) {
 void table_add(const std::string& key, const TuneChoice& c) {
     std::lock_guard<std::mutex> lk(g_table_mu);
     load_table_locked();
-    g_table->push_back({key, c.variant, c.slices, c.threads, c.ms});
+    g_table->push_back({key, c.variant, c.slices, c.threads, c.ms, c.sweep_bin});
     const char* path = getenv("KH_TUNE_FILE");
     if (!path || !*path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s | %d %d %d %.4f\n", key.c_str(), c.variant, c.slices, c.threads, c.ms);
+    fprintf(f, "%s | %d %d %d %.4f %d\n", key.c_str(), c.variant, c.slices, c.threads, c.ms, c.sweep_bin);
     fclose(f);
 }
 
@@ -225,12 +228,69 @@ int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out) {
         t.ms = ms;
         if (ms >= 0.0 && ms < best.ms) best = t;
     }
-    g.launches = launches_before;  // tuning launches are not the caller's work
     if (best.variant == KH_VAR_AUTO) {
         // nothing measured (no sources): any valid layout does
-        best = cta_fits(g) ? TuneChoice{KH_VAR_CTA, 0, 256, 0.0}
-                           : TuneChoice{KH_VAR_SLICED, s0, 1024, 0.0};
+        best = cta_fits(g) ? TuneChoice{KH_VAR_CTA, 0, 256, 0.0, 0}
+                           : TuneChoice{KH_VAR_SLICED, s0, 1024, 0.0, 0};
     }
+    // Bit-parallel sweeps for the sources of 2-hop work >= 2^b - 1, the
+    // sliced layout for the rest: the number of sweeps times the time of the
+    // middle sweep of the range (a sweep's cost hardly depends on its batch,
+    // except for the first few, whose sources' own rows are the longest),
+    // plus the sliced layout's time on the sample's remaining sources scaled
+    // by the stride, against the sliced layout alone on the whole sample,
+    // likewise scaled.
+    best.sweep_bin = 0;
+    if (best.variant != KH_VAR_CTA && m > 0 && hdeg2_sources_from_bin(g, kSweepMinBin) > 0) {
+        auto time_sweep = [&](int64_t first, int64_t nb) -> double {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            double t = -1.0;
+            if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                for (int rep = 0; rep < 2; ++rep) {  // the first run also builds the sweep arrays
+                    cudaEventRecord(e0, s);
+                    const int rc2 = run_sweeps(g, scratch, g.order2 + first, nb, s);
+                    cudaEventRecord(e1, s);
+                    float ms = 0.f;
+                    if (rc2 != KH_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        t = -1.0;
+                        break;
+                    }
+                    t = ms;
+                }
+            } else {
+                cudaGetLastError();
+            }
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            return t;
+        };
+        const double t_warm = time_sweep(0, std::min<int64_t>(g.nsrc2, 128));  // builds the arrays
+        const double t_none = best.ms * (double)stride;
+        double t_best = t_none;
+        for (int bin = kOrderBinsMax - 1; t_warm >= 0.0 && bin >= kSweepMinBin; --bin) {
+            const int64_t nsw = hdeg2_sources_from_bin(g, bin);
+            if (nsw == 0) continue;
+            if (nsw >= g.nsrc2) break;
+            const int64_t sbig = (nsw + stride - 1) / stride;  // sample entries that are swept
+            if (sbig >= m) break;
+            const int64_t nb_mid = std::min<int64_t>(nsw, 128);
+            const int64_t mid = ((nsw / 2) / 128) * 128;
+            const double t_mid = time_sweep(mid + nb_mid <= nsw ? mid : nsw - nb_mid, nb_mid);
+            if (t_mid < 0.0) break;
+            TuneChoice rest = best;
+            const double t_rest = time_candidate(g, rest, sample + sbig, d_count, m - sbig, scratch, s,
+                                                 sample_big > sbig ? sample_big - sbig : 0);
+            if (t_rest < 0.0) break;
+            const double t = (double)((nsw + 127) / 128) * t_mid + t_rest * (double)stride;
+            if (t < t_best) {
+                t_best = t;
+                best.sweep_bin = bin;
+            }
+        }
+    }
+    g.launches = launches_before;  // tuning launches are not the caller's work
     g.tuned_hdeg2 = best;
     table_add(key, best);
     *out = best;
@@ -245,7 +305,16 @@ int run_hdeg_full(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cudaStr
         if (c.variant == KH_VAR_SLICED || c.variant == KH_VAR_SLICED_SMALL) {
             rc = ensure_order2(g, s);
             if (rc) return rc;
-            return run_sliced(g, c, deg, cnt, jlo, nj, s, g.order2, g.nsrc2, hdeg2_small_split(g));
+            // the sources of largest 2-hop work go to the bit-parallel sweeps
+            // (2-degrees only: the fixed-level counts stay with the sliced kernel)
+            int bin = g.sw_force != 0 ? g.sw_force : c.sweep_bin;
+            if (cnt || bin < 0) bin = 0;
+            int64_t nsw = bin > 0 ? hdeg2_sources_from_bin(g, bin) : 0;
+            const int64_t big = hdeg2_small_split(g);
+            rc = run_sliced(g, c, deg, cnt, jlo, nj, s, g.order2 + nsw, g.nsrc2 - nsw,
+                            big > nsw ? big - nsw : 0);
+            if (rc || nsw == 0) return rc;
+            return run_sweeps(g, deg, g.order2, nsw, s);
         }
     }
     return launch_hdeg(g, nullptr, nullptr, g.n, deg, cnt, jlo, nj, s);
@@ -268,6 +337,21 @@ extern "C" int kh_set_variant(kh_graph* G, int32_t op, int32_t variant, int32_t 
             variant != KH_LEVELU_GROUPED)
             return kh::set_error(g.ctx, KH_EINVAL, "unknown union schedule %d", variant);
         g.levelu_mode = variant;
+        return KH_OK;
+    }
+    if (op == KH_OP_HDEG2_SWEEP) {
+        if (variant == KH_VAR_AUTO) {
+            g.sw_force = 0;
+        } else if (variant == KH_SWEEP_OFF) {
+            g.sw_force = -1;
+        } else if (variant == KH_SWEEP_FROM) {
+            if (slices < 1 || slices >= kh::kOrderBinsMax)
+                return kh::set_error(g.ctx, KH_EINVAL, "sweep work bin %d outside [1, %d)", slices,
+                                     kh::kOrderBinsMax);
+            g.sw_force = slices;
+        } else {
+            return kh::set_error(g.ctx, KH_EINVAL, "unknown sweep setting %d", variant);
+        }
         return KH_OK;
     }
     if (op != KH_OP_HDEG2) return kh::set_error(g.ctx, KH_EINVAL, "unknown operation %d", op);
@@ -304,6 +388,8 @@ extern "C" int kh_get_variant(kh_graph* G, int32_t op, int32_t* variant, int32_t
         if (tuned_ms) *tuned_ms = 0.0;
         return KH_OK;
     }
+    const bool sweep_op = op == KH_OP_HDEG2_SWEEP;
+    if (sweep_op) op = KH_OP_HDEG2;
     if (op != KH_OP_HDEG2) return kh::set_error(g.ctx, KH_EINVAL, "unknown operation %d", op);
     cudaSetDevice(g.ctx->device);
     kh::TuneChoice c{};
@@ -315,6 +401,15 @@ extern "C" int kh_get_variant(kh_graph* G, int32_t op, int32_t* variant, int32_t
     }
     rc = kh::choose_hdeg2(g, g.ctx->stream, &c);
     if (rc) return rc;
+    if (sweep_op) {
+        // the sweep setting in force: off, or the work bin it starts from
+        const int bin = g.sw_force != 0 ? g.sw_force : c.sweep_bin;
+        if (variant) *variant = bin > 0 ? KH_SWEEP_FROM : KH_SWEEP_OFF;
+        if (slices) *slices = bin > 0 ? bin : 0;
+        if (threads) *threads = 0;
+        if (tuned_ms) *tuned_ms = c.ms;
+        return KH_OK;
+    }
     if (variant) *variant = c.variant;
     if (slices) *slices = c.slices;
     if (threads) *threads = c.threads;

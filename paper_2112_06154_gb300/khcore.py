@@ -41,6 +41,9 @@ KH_OP_LEVEL_UNION = 2
 KH_LEVELU_STEPPED = 1
 KH_LEVELU_FREE = 2
 KH_LEVELU_GROUPED = 3
+KH_OP_HDEG2_SWEEP = 3
+KH_SWEEP_OFF = 1
+KH_SWEEP_FROM = 2
 PROF_NAMES = ["bfs", "level1", "levelU", "frontier", "peel"]
 
 _ERRNAMES = {KH_EINVAL: "KH_EINVAL", KH_EGRAPH: "KH_EGRAPH", KH_ENOMEM: "KH_ENOMEM",
@@ -81,6 +84,7 @@ SIGNATURES = [
     ("kh_dense_pruned", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_double,
                                        _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
     ("kh_prof_trace", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
+    ("kh_prof_trace_bytes", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _I64P]),
     ("kh_launch_count", ctypes.c_int, [_P, _I64P]),
     ("kh_hdegree_exact_noalloc", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.c_int32, _P, _P]),
     ("kh_set_variant", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -406,6 +410,17 @@ def kh_prof_trace(g: Graph, kind: int) -> np.ndarray:
     return out[:n.value]
 
 
+def kh_prof_trace_bytes(g: Graph, kind: int) -> np.ndarray:
+    """Algorithmic bytes of every bracketed launch of one kernel class, in the
+    order of kh_prof_trace (UINT64_MAX where not recorded)."""
+    n = ctypes.c_int64()
+    _check(load().kh_prof_trace_bytes(g.handle, kind, None, 0, ctypes.byref(n)), g.ctx)
+    out = np.zeros(max(n.value, 1), np.uint64)
+    _check(load().kh_prof_trace_bytes(g.handle, kind, out.ctypes.data, out.size, ctypes.byref(n)),
+           g.ctx)
+    return out[:n.value]
+
+
 def kh_launch_count(g: Graph) -> int:
     n = ctypes.c_int64()
     _check(load().kh_launch_count(g.handle, ctypes.byref(n)), g.ctx)
@@ -415,7 +430,9 @@ def kh_launch_count(g: Graph) -> int:
 def kh_set_variant(g: Graph, variant: int, slices: int = 0, threads: int = 0,
                    op: int = KH_OP_HDEG2):
     """Force the layout of the h = 2 exact-degree pass (KH_VAR_AUTO: the tuner's),
-    or (op=KH_OP_PEEL_COMPACT) the peel's compaction setting."""
+    or another schedule setting by op: KH_OP_PEEL_COMPACT (compaction),
+    KH_OP_LEVEL_UNION (level union), KH_OP_HDEG2_SWEEP (bit-parallel sweeps;
+    KH_SWEEP_FROM with slices = the work bin)."""
     _check(load().kh_set_variant(g.handle, op, variant, slices, threads), g.ctx)
 
 

@@ -54,6 +54,7 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert K.load().kh_last_error(None) == b"null context"
     assert K.load().kh_peel_stats(None, None, None, None) == K.KH_EINVAL
     assert K.load().kh_prof_trace(None, 0, None, 0, None) == K.KH_EINVAL
+    assert K.load().kh_prof_trace_bytes(None, 0, None, 0, None) == K.KH_EINVAL
     assert K.load().kh_debug_fail_alloc(None, 1) == K.KH_EINVAL
 
 

@@ -1,4 +1,4 @@
-"""The two layouts of the whole-graph exact 2-degree pass and their autotuner.
+"""The layouts of the whole-graph exact 2-degree pass and their autotuner.
 
 Every forced layout (one CTA per source; (source, slice) items with 1..64
 slices and 128..1024 threads per CTA; the same with the sources of small
@@ -6,6 +6,9 @@ slices and 128..1024 threads per CTA; the same with the sources of small
 and fixed-level counts element by element, on graphs with isolated nodes,
 ragged slice tails, hubs, and 2-hop work on both sides of the warp kernel's
 limit (stars of 510 and 512 leaves); the tuner's choice must be one of them.
+The bit-parallel sweeps for the sources of largest 2-hop work must give the
+same degrees for every threshold, with batches of 128 sources, a ragged last
+batch, and rows long enough for the sweep's tail pieces.
 """
 import os
 import subprocess
@@ -80,6 +83,60 @@ def test_every_layout_matches_the_oracle(ctx, name):
         var, sl, th, ms = K.kh_get_variant(G)
         assert var in (K.KH_VAR_CTA, K.KH_VAR_SLICED, K.KH_VAR_SLICED_SMALL) and ms >= 0.0
         assert (K.kh_hdegree_exact(G) == want).all()
+    finally:
+        G.close()
+
+
+SWEEP_GRAPHS = {
+    "er": lambda: gg.erdos_renyi(2000, 8000, 1001),
+    "ragged": _ragged,
+    "cl20k": lambda: gg.chung_lu(20000, 20, 2.5, 1500, 1102),
+    "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 7),
+    # rows longer than the sweep kernel's head of 512 entries: one tail piece
+    # (a star of 1500 leaves), several pieces (hubs of 9000 / 6000 / 4500)
+    "star1500": lambda: gg.star(1500),
+    "hubs": lambda: gg.with_hubs(12000, (9000, 6000, 4500), 77),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SWEEP_GRAPHS))
+def test_bit_parallel_sweeps_match_the_oracle(ctx, name):
+    rp, cl = SWEEP_GRAPHS[name]()
+    n = rp.size - 1
+    want = O.hdegree_exact(rp, cl, 2)
+    r = O.ranks(n, 1)
+    want_cnt = O.fixed_counts(rp, cl, r, 2, 0, 10)
+    G = K.kh_graph_load_csr(ctx, rp, cl)
+    try:
+        K.kh_set_h(G, 2)
+        # every source with 2-hop work >= 2^b - 1 is swept (b = 1: every
+        # non-isolated source, in batches of 128 and a ragged last batch)
+        for var, th in ((K.KH_VAR_SLICED, 256), (K.KH_VAR_SLICED_SMALL, 1024)):
+            K.kh_set_variant(G, var, 2, th)
+            for b in (1, 5, 8, 11, 14):
+                K.kh_set_variant(G, K.KH_SWEEP_FROM, b, 0, op=K.KH_OP_HDEG2_SWEEP)
+                assert (K.kh_hdegree_exact(G) == want).all(), (var, b)
+                v, sb, _, _ = K.kh_get_variant(G, op=K.KH_OP_HDEG2_SWEEP)
+                assert v == K.KH_SWEEP_FROM and sb == b
+            # the fixed-level counts do not use the sweeps
+            assert (K.kh_sampled_counts(G, 0, 10) == want_cnt).all()
+            K.kh_set_variant(G, K.KH_SWEEP_OFF, op=K.KH_OP_HDEG2_SWEEP)
+            assert (K.kh_hdegree_exact(G) == want).all()
+            assert K.kh_get_variant(G, op=K.KH_OP_HDEG2_SWEEP)[0] == K.KH_SWEEP_OFF
+        K.kh_set_variant(G, K.KH_VAR_AUTO, op=K.KH_OP_HDEG2_SWEEP)
+        K.kh_set_variant(G, K.KH_VAR_AUTO)
+        assert (K.kh_hdegree_exact(G) == want).all()
+    finally:
+        G.close()
+
+
+def test_sweep_arguments_are_checked(ctx):
+    rp, cl = gg.erdos_renyi(2000, 8000, 1001)
+    G = K.kh_graph_load_csr(ctx, rp, cl)
+    try:
+        for args in [(K.KH_SWEEP_FROM, 0), (K.KH_SWEEP_FROM, 48), (9, 3)]:
+            with pytest.raises(K.KhError):
+                K.kh_set_variant(G, args[0], args[1], 0, op=K.KH_OP_HDEG2_SWEEP)
     finally:
         G.close()
 

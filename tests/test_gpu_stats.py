@@ -40,10 +40,14 @@ def test_sampled_peel_stats(ctx, h):
         assert ref[h:].sum() == 0
         # early-stopped refines leave a lower bound only: counted apart from updates
         assert stopped >= 0 and updates > 0
-        ms, launches, _ = K.kh_prof_read(G, K.KH_PROF_LEVELU)
+        ms, launches, alg = K.kh_prof_read(G, K.KH_PROF_LEVELU)
         trace = K.kh_prof_trace(G, K.KH_PROF_LEVELU)
         assert trace.size == launches > 0
         assert abs(float(trace.sum()) - ms) <= 1e-3 * max(ms, 1.0)
+        # per-launch algorithmic bytes add up to the class counter
+        tb = K.kh_prof_trace_bytes(G, K.KH_PROF_LEVELU)
+        assert tb.size == launches and (tb != np.uint64(2**64 - 1)).all()
+        assert int(tb.sum()) == int(alg)
         # the launch-by-launch (profiled) peel and the graph replay agree
         K.kh_prof_enable(G, False)
         assert (K.kh_core_sampled(G) == core).all()
