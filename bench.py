@@ -46,7 +46,7 @@ E2E_STEPS = 3  # end-to-end steps (graph upload included), capped to keep the ru
 
 # kernel class -> the kernels it brackets (kh_prof_read kinds)
 CLASS_KERNELS = {
-    "bfs": "k_hdeg / k_hdeg2_slice (exact h-degree BFS)",
+    "bfs": "k_hdeg, k_hdeg2_slice, k_hdeg2_small, k_sweep_* (exact h-degrees)",
     "level1": "k_level1, k_level1_heavy (level-1 lists)",
     "levelU": "k_levelU (level >= 2 lists, hashed union with trim)",
     "frontier": "k_mark_nbrs, k_ball_hop, k_stale_*, k_apply_loss",

@@ -10,7 +10,13 @@ Rank filter (sampled refresh): level i of v is the rank filter of the union
 of its neighbours' level i-1 lists (Prop. 3.1, Alg. 2), so if v has no
 removed neighbour and every changed neighbour list w has rho_w < k[v,i] - 1
 (rho_w: the top rank among the members that left, or k_old[w] - 1 when the
-level of w fell), then B[v,i] and k[v,i] do not change."""
+level of w fell), then B[v,i] and k[v,i] do not change.
+
+Bit-parallel 2-balls (sweeps of the exact 2-degree pass): with m1[u] = {j : u
+in A(s_j)} for a batch of sources s_j, x is in N(s_j; 2) exactly when j is in
+m1[x] | OR_{u in A(x)} m1[u]; and a filter with one bit per group of 4 node
+ids, set for every group holding a node with m1 != {}, never drops an entry
+that contributes."""
 import numpy as np
 import pytest
 from scipy.sparse import csr_matrix
@@ -113,3 +119,36 @@ def test_rank_filter_never_skips_a_change(h, M):
                     rho[int(v)] = t
                 prev_rho = rho
             X = Xn
+
+
+def test_bit_parallel_two_balls_equal_the_definition():
+    rng = np.random.default_rng(11)
+    for rowptr, col in graphs():
+        n = rowptr.size - 1
+        deg = np.diff(rowptr)
+        src_all = np.nonzero(deg > 0)[0]
+        batch = rng.choice(src_all, min(40, src_all.size), replace=False)
+        # m1 as Python ints (bit j per source), filter per 4-id group
+        m1 = [0] * n
+        for j, s_ in enumerate(batch):
+            for u in col[rowptr[s_]:rowptr[s_ + 1]]:
+                m1[u] |= 1 << j
+        filt = np.zeros((n + 3) // 4, bool)
+        for u in range(n):
+            if m1[u]:
+                filt[u >> 2] = True
+        ball = [0] * n
+        for x in range(n):
+            if deg[x] == 0:
+                continue
+            b = m1[x]
+            for u in col[rowptr[x]:rowptr[x + 1]]:
+                if filt[u >> 2]:
+                    b |= m1[u]
+                else:
+                    assert m1[u] == 0  # the filter only drops entries with no source bits
+            ball[x] = b
+        want = O.hdegree_exact(rowptr, col, 2)
+        for j, s_ in enumerate(batch):
+            members = sum(1 for x in range(n) if (ball[x] >> j) & 1)
+            assert members - 1 == want[s_], (j, s_)
