@@ -176,8 +176,10 @@ def parse():
     p.add_argument("--sweep", default=None,
                    help="--op hdeg2 only: 'off', or a work bin b: sources of 2-hop work >= 2^b - 1 "
                         "go to the bit-parallel sweeps (default: the tuner's choice)")
-    p.add_argument("--union", choices=["auto", "stepped", "free", "grouped"], default="auto",
-                   help="schedule of the level-union kernel (kh_set_variant KH_OP_LEVEL_UNION)")
+    p.add_argument("--union", default="auto",
+                   help="schedule of the level-union kernel (kh_set_variant KH_OP_LEVEL_UNION): "
+                        "auto, stepped, free, grouped or grouped:D (a lane group covers 1/D of "
+                        "a list's expected keys)")
     p.add_argument("--prof", action="store_true",
                    help="--op only: bracket the kernel classes and print their times and "
                         "algorithmic bytes")
@@ -194,7 +196,8 @@ def parse():
 def apply_union(K, G, args):
     mode = {"auto": K.KH_VAR_AUTO, "stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE,
             "grouped": K.KH_LEVELU_GROUPED}
-    K.kh_set_variant(G, mode[getattr(args, "union", "auto")], op=K.KH_OP_LEVEL_UNION)
+    name, _, div = getattr(args, "union", "auto").partition(":")
+    K.kh_set_variant(G, mode[name], int(div or 0), op=K.KH_OP_LEVEL_UNION)
 
 
 def dist_env():

@@ -305,7 +305,9 @@ int kh_hdegree_exact_noalloc(int64_t n, const int64_t *rowptr, const int32_t *co
  * lists in place of whole warps: per node, the fewest lanes whose step of
  * 4 keys a lane covers the keys a list is expected to give at or above the
  * starting level (sum of |B[w]| 2^(k[w] - t) over the lists, over their
- * number).  KH_VAR_AUTO: grouped.  The lists are the same every way. */
+ * number); with slices = d > 1 (a power of two up to 64) a group covers 1/d
+ * of those keys (0: the default).  KH_VAR_AUTO: grouped.  The lists are the
+ * same every way. */
 #define KH_OP_LEVEL_UNION 2
 #define KH_LEVELU_STEPPED 1
 #define KH_LEVELU_FREE 2

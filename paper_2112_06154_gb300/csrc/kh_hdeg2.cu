@@ -381,38 +381,37 @@ __global__ void k_init2(const int64_t* __restrict__ rowptr, const uint8_t* __res
 // skips the gathers of entries that cannot contribute: for batches of
 // mid-size sources half of all entries or more.
 constexpr int kSweepSrc = 128;
-constexpr int kSweepHead = 512;    // row entries the count kernel reads itself
+constexpr int kSweepHead = 64;     // row entries the count kernel reads itself (8 per lane)
 constexpr int kSweepPiece = 2048;  // entries per tail piece of a longer row
 constexpr int kSweepPlanes = 8;    // carry-save counter planes: 255 additions between flushes
 
 // Set (clear = 0) or zero (clear = 1) the batch's source bits on the
-// neighbours of its sources; the setting pass also counts each source's
+// neighbours of its sources, one CTA per source (the largest sources' rows
+// hold up to the maximum degree); the setting pass also counts each source's
 // algorithmic bytes (those of one 2-hop search).
 __global__ void k_sweep_scatter(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                 const int32_t* __restrict__ src, int nb, uint32_t* __restrict__ m1,
                                 uint32_t* __restrict__ filter, int clear, unsigned long long* bytes) {
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int j = blockIdx.x;
+    if (j >= nb) return;
+    const int v = src[j];
+    const int64_t b = rowptr[v], e = rowptr[v + 1];
     unsigned long long my = 0;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nb; j += nw) {
-        const int v = src[j];
-        const int64_t b = rowptr[v], e = rowptr[v + 1];
-        for (int64_t k = b + lane; k < e; k += 32) {
-            const int32_t u = __ldg(col + k);
-            if (clear) {
-                reinterpret_cast<uint4*>(m1)[u] = make_uint4(0u, 0u, 0u, 0u);
-                filter[u >> 7] = 0u;
-            } else {
-                atomicOr(m1 + 4 * (size_t)u + (j >> 5), 1u << (j & 31));
-                atomicOr(filter + (u >> 7), 1u << ((u >> 2) & 31));
-                my += 8ull + 4ull * (unsigned long long)(rowptr[u + 1] - rowptr[u]);
-            }
+    for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+        const int32_t u = __ldg(col + k);
+        if (clear) {
+            reinterpret_cast<uint4*>(m1)[u] = make_uint4(0u, 0u, 0u, 0u);
+            filter[u >> 7] = 0u;
+        } else {
+            atomicOr(m1 + 4 * (size_t)u + (j >> 5), 1u << (j & 31));
+            atomicOr(filter + (u >> 7), 1u << ((u >> 2) & 31));
+            my += 8ull + 4ull * (unsigned long long)(rowptr[u + 1] - rowptr[u]);
         }
-        if (!clear && lane == 0) my += 8ull + 4ull * (unsigned long long)(e - b) + 4ull;
     }
     if (clear) return;
+    if (threadIdx.x == 0) my += 8ull + 4ull * (unsigned long long)(e - b) + 4ull;
     for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(kFull, my, off);
-    if (lane == 0 && my) atomicAdd(bytes, my);
+    if ((threadIdx.x & 31) == 0 && my) atomicAdd(bytes, my);
 }
 
 __device__ __forceinline__ void or4(uint4& a, const uint4 b) {
@@ -732,7 +731,7 @@ int run_sweeps(Graph& g, int32_t* deg, const int32_t* src, int64_t count, cudaSt
     int64_t sweeps = 0;
     for (int64_t b0 = 0; b0 < count; b0 += kSweepSrc, ++sweeps) {
         const int nb = (int)(count - b0 < kSweepSrc ? count - b0 : kSweepSrc);
-        const int sgrid = (nb + 7) / 8;
+        const int sgrid = nb;
         k_sweep_scatter<<<sgrid, 256, 0, s>>>(g.rowptr, g.col, src + b0, nb, g.sw_m1, g.sw_filter, 0,
                                               &g.state->bytes[kProfBfs]);
         if (g.sw_npieces > 0) {

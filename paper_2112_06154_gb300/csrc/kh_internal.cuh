@@ -352,6 +352,7 @@ struct Graph {
     int64_t vcount;
     int compact_mode;       // KH_VAR_AUTO, KH_COMPACT_OFF or KH_COMPACT_ALWAYS
     int levelu_mode;        // KH_VAR_AUTO (grouped), KH_LEVELU_STEPPED, _FREE or _GROUPED
+    int levelu_div;         // grouped: coverage divisor (0: the default)
     int cp_cur;             // buffer set in use (0 or 1)
     int64_t *cp_row[2];
     int32_t *cp_col[2];

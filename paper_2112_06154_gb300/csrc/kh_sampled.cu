@@ -57,7 +57,8 @@ struct LevelArgs {
     const int* d_count;
     int64_t count_static;
     int track;
-    int group_lists;           // free union: lanes per list by the list count (else a warp)
+    int group_lists;           // free union: lane groups per list (0: a warp per list)
+    int group_div;             // grouped: a group covers 1/group_div of the expected keys
     int32_t* changed;
     int* n_changed;
     int32_t* heavy;            // level 1: nodes of degree > kL1Heavy, for the CTA kernel
@@ -408,26 +409,41 @@ __device__ __forceinline__ bool set_contains(const uint32_t* tab, int lg, uint32
     return false;
 }
 
+// Grouped union: a lane group's step covers 1/kGroupDivDefault of the keys a
+// list is expected to give (the rest take further steps).
+constexpr int kGroupDivDefault = 1;
+
 // Keys one thread loads per step (one 16-byte vector); a warp's chunk.
 constexpr int kKeysPerLane = 4;
 constexpr int kChunkKeys = 32 * kKeysPerLane;
 // Nodes up to this degree use the flat (list, chunk) schedule of k_levelU.
 constexpr int kFlatMax = kLuThreads;
 
-// Shared memory of k_levelU for a table of 2^lg slots: keys, compaction
-// stage (half size), and the list of used slots (16-bit indices).
-size_t levelU_smem(int lg) {
+// Shared memory of k_levelU for a table of 2^lg slots: keys, the compaction
+// stage (scap keys: a compaction keeps the keys at or above the level trimmed
+// from the complete counts, at most M), and the list of used slots (16-bit
+// indices; a set holds at most half its slots plus what the warps insert
+// before they stop for a compaction, under 2048).
+__host__ __device__ __forceinline__ int levelU_used_cap(int hcap) { return (hcap >> 1) + 2048; }
+
+int levelU_stage_cap(int lg, int64_t M) {
+    const int64_t half = (int64_t)1 << (lg - 1);
+    const int64_t need = (M + 64 + 3) & ~(int64_t)3;
+    return (int)(need < half ? need : half);
+}
+
+size_t levelU_smem(int lg, int scap) {
     const size_t hcap = (size_t)1 << lg;
-    return hcap * 4 + (hcap >> 1) * 4 + hcap * 2;
+    return hcap * 4 + (size_t)scap * 4 + (size_t)levelU_used_cap((int)hcap) * 2;
 }
 
 // Drop the keys below t from the hash set: empty their slots, re-insert the
 // rest (all threads of the CTA).
 __device__ __forceinline__ void compact_set(uint32_t* tab, uint32_t* stage, uint16_t* used, int lg,
-                                            int hcap, int tc, int* s_nused, int* s_nstage,
-                                            int* err) {
+                                            int scap, int ucap, int tc, int* s_nused,
+                                            int* s_nstage, int* err) {
     const int tid = threadIdx.x;
-    const int nu = min(*s_nused, hcap);
+    const int nu = min(*s_nused, ucap);
     if (tid == 0) *s_nstage = 0;
     __syncthreads();
     for (int i = tid; i < nu; i += blockDim.x) {
@@ -436,14 +452,14 @@ __device__ __forceinline__ void compact_set(uint32_t* tab, uint32_t* stage, uint
         tab[slot] = kEmpty;
         if ((int)(key >> kIdBits) >= tc) {
             const int p = atomicAdd(s_nstage, 1);
-            if (p < (hcap >> 1)) stage[p] = key;
+            if (p < scap) stage[p] = key;
             else atomicOr(err, kErrProbe);
         }
     }
     __syncthreads();
     if (tid == 0) *s_nused = 0;
     __syncthreads();
-    const int ns = min(*s_nstage, hcap >> 1);
+    const int ns = min(*s_nstage, scap);
     for (int i = tid; i < ns; i += blockDim.x) {
         const int slot = set_insert(tab, lg, stage[i], err);
         if (slot >= 0) used[atomicAdd(s_nused, 1)] = (uint16_t)slot;
@@ -480,6 +496,7 @@ __device__ __forceinline__ int snapshot_counts(const int* s_hist, int lane) {
 // Returns true when the refine stopped early (s_part holds the bound).
 __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& nl, uint32_t* tab,
                                         uint32_t* stage, uint16_t* used, int lg, int hcap,
+                                        int scap, int ucap,
                                         int* s_hist, int* s_t, int* s_nused, int* s_nstage,
                                         int* s_exit, unsigned long long* s_part, int* s_item,
                                         int* s_creq, unsigned long long T, int vin, bool can_stop,
@@ -558,17 +575,17 @@ __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& 
                 const uint4 k4 = mode == 2 ? __ldcg(reinterpret_cast<const uint4*>(clp + p))
                                            : *reinterpret_cast<const uint4*>(clp + p);
                 const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+                if (mode != 2) my_bytes += 4ull * (unsigned long long)min(kKeysPerLane, csz - p);
 #pragma unroll
                 for (int q = 0; q < kKeysPerLane; ++q) {
                     if (p + q < csz) {
                         const uint32_t key = kk[q];
                         const int r = (int)(key >> kIdBits);
-                        if (mode != 2) my_bytes += 4;
                         if (r >= t) {
                             const int slot = set_insert(tab, lg, key, a.err);
                             if (slot >= 0) {
                                 const int u = atomicAdd(s_nused, 1);
-                                if (u < hcap) used[u] = (uint16_t)slot;
+                                if (u < ucap) used[u] = (uint16_t)slot;
                                 else atomicOr(a.err, kErrProbe);
                                 atomicAdd(&s_hist[r], 1);
                             }
@@ -616,7 +633,7 @@ __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& 
             if (lane == 0 && pmax + 1 > *s_t) *s_t = pmax + 1;
         }
         __syncthreads();
-        compact_set(tab, stage, used, lg, hcap, *s_t, s_nused, s_nstage, a.err);
+        compact_set(tab, stage, used, lg, scap, ucap, *s_t, s_nused, s_nstage, a.err);
         if (tid == 0) *s_creq = 0;
         __syncthreads();
     }
@@ -643,12 +660,13 @@ __device__ __forceinline__ bool free_union(const LevelArgs& a, const NodeLevel& 
 // FREE: the union's warps run free instead of in barrier-separated steps (see
 // the FREE branch below); both give the same lists.
 template <bool FREE>
-__global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
+__global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg, int scap) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     const int hcap = 1 << lg;
+    const int ucap = levelU_used_cap(hcap);
     uint32_t* tab = s_dyn;
-    uint32_t* stage = s_dyn + hcap;                                        // hcap / 2 keys
-    uint16_t* used = reinterpret_cast<uint16_t*>(s_dyn + hcap + (hcap >> 1));  // hcap slots
+    uint32_t* stage = s_dyn + hcap;                                         // scap keys
+    uint16_t* used = reinterpret_cast<uint16_t*>(s_dyn + hcap + scap);      // ucap slots
     __shared__ int s_hist[32];
     __shared__ int s_src, s_t, s_nused, s_nstage, s_compact;
     __shared__ int s_vin, s_exit;                // own key in the table; early stop taken
@@ -770,9 +788,10 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
                 int G = 32;
                 if (a.group_lists) {
                     const float per = s_ex / (float)(1u << (s_t & 31)) / (float)(L > 0 ? L : 1);
-                    while (G > 1 && (float)(kKeysPerLane * (G >> 1)) >= per) G >>= 1;
+                    while (G > 1 && (float)(kKeysPerLane * (G >> 1) * a.group_div) >= per) G >>= 1;
                 }
-                stopped = free_union(a, nl, tab, stage, used, lg, hcap, s_hist, &s_t, &s_nused,
+                stopped = free_union(a, nl, tab, stage, used, lg, hcap, scap, ucap, s_hist, &s_t,
+                                     &s_nused,
                                      &s_nstage, &s_exit, &s_part, &s_item, &s_creq, s_T, s_vin,
                                      can_stop, mode, first, b, l0, L, rv, G, my_bytes);
             } else {
@@ -852,7 +871,7 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
                                             const int slot = set_insert(tab, lg, key, a.err);
                                             if (slot >= 0) {
                                                 const int u = atomicAdd(&s_nused, 1);
-                                                if (u < hcap) used[u] = (uint16_t)slot;
+                                                if (u < ucap) used[u] = (uint16_t)slot;
                                                 else atomicOr(a.err, kErrProbe);
                                                 atomicAdd(&s_hist[r], 1);
                                             }
@@ -904,7 +923,7 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
                                     const int slot = set_insert(tab, lg, key, a.err);
                                     if (slot >= 0) {
                                         const int u = atomicAdd(&s_nused, 1);
-                                        if (u < hcap) used[u] = (uint16_t)slot;
+                                        if (u < ucap) used[u] = (uint16_t)slot;
                                         else atomicOr(a.err, kErrProbe);
                                         atomicAdd(&s_hist[r], 1);
                                     }
@@ -966,21 +985,21 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
                 }
                 if (s_compact) {
                     // drop keys below t: empty their slots, re-insert the rest
-                    const int tc = s_t, nu = min(s_nused, hcap);
+                    const int tc = s_t, nu = min(s_nused, ucap);
                     for (int i = tid; i < nu; i += blockDim.x) {
                         const int slot = used[i];
                         const uint32_t key = tab[slot];
                         tab[slot] = kEmpty;
                         if ((int)(key >> kIdBits) >= tc) {
                             const int p = atomicAdd(&s_nstage, 1);
-                            if (p < (hcap >> 1)) stage[p] = key;
+                            if (p < scap) stage[p] = key;
                             else atomicOr(a.err, kErrProbe);
                         }
                     }
                     __syncthreads();
                     if (tid == 0) s_nused = 0;
                     __syncthreads();
-                    const int ns = min(s_nstage, hcap >> 1);
+                    const int ns = min(s_nstage, scap);
                     for (int i = tid; i < ns; i += blockDim.x) {
                         const int slot = set_insert(tab, lg, stage[i], a.err);
                         if (slot >= 0) used[atomicAdd(&s_nused, 1)] = (uint16_t)slot;
@@ -991,7 +1010,7 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
             }  // stepped union
             if (stopped) {
                 // d(v) > T: v stays stale, its lower bound raised to the partial estimate
-                const int nu = min(s_nused, hcap);
+                const int nu = min(s_nused, ucap);
                 for (int i = tid; i < nu; i += blockDim.x) tab[used[i]] = kEmpty;
                 if (mode == 0) {
                     if (tid == 0) {
@@ -1010,7 +1029,7 @@ __global__ void __launch_bounds__(kLuThreads, 6) k_levelU(LevelArgs a, int lg) {
                 }
             }
             const int kappa = s_t;
-            const int nu = min(s_nused, hcap);
+            const int nu = min(s_nused, ucap);
             int S = 0;
             for (int j = kappa; j < 32; ++j) S += s_hist[j];
             __syncthreads();
@@ -1583,11 +1602,14 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     if (!wantU) return KH_OK;
     a.bytes = &g.state->bytes[kProfLevelU];
     const int lg = table_lg(g.M);
-    const size_t dyn = levelU_smem(lg);
+    const int scap = levelU_stage_cap(lg, g.M);
+    const size_t dyn = levelU_smem(lg, scap);
     // free-running lane groups unless another schedule is asked for (grouped
     // is the fastest, or within 2%, on every measured workload)
-    void (*kern)(LevelArgs, int) = g.levelu_mode == KH_LEVELU_STEPPED ? k_levelU<false> : k_levelU<true>;
+    void (*kern)(LevelArgs, int, int) =
+        g.levelu_mode == KH_LEVELU_STEPPED ? k_levelU<false> : k_levelU<true>;
     a.group_lists = g.levelu_mode == KH_LEVELU_FREE ? 0 : 1;
+    a.group_div = g.levelu_div > 0 ? g.levelu_div : kGroupDivDefault;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
     int per_sm = 0;
@@ -1615,7 +1637,7 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
     } else {
         a.n_sub = nullptr;
     }
-    kern<<<(int)grid, kLuThreads, dyn, s>>>(a, lg);
+    kern<<<(int)grid, kLuThreads, dyn, s>>>(a, lg, scap);
     count_launch(g, 1);
     prof_end(g, kProfLevelU, s);
     return KH_OK;

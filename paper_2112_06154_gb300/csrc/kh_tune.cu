@@ -240,8 +240,11 @@ int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out) {
     // plus the sliced layout's time on the sample's remaining sources scaled
     // by the stride, against the sliced layout alone on the whole sample,
     // likewise scaled.
+    // (only where the whole pass takes 20 ms or more, and only for a predicted
+    // gain of 5%: on small graphs the sample times are too short to rank them)
     best.sweep_bin = 0;
-    if (best.variant != KH_VAR_CTA && m > 0 && hdeg2_sources_from_bin(g, kSweepMinBin) > 0) {
+    if (best.variant != KH_VAR_CTA && m > 0 && hdeg2_sources_from_bin(g, kSweepMinBin) > 0 &&
+        best.ms * (double)stride >= 20.0) {
         auto time_sweep = [&](int64_t first, int64_t nb) -> double {
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             double t = -1.0;
@@ -268,7 +271,7 @@ int choose_hdeg2(Graph& g, cudaStream_t s, TuneChoice* out) {
         };
         const double t_warm = time_sweep(0, std::min<int64_t>(g.nsrc2, 128));  // builds the arrays
         const double t_none = best.ms * (double)stride;
-        double t_best = t_none;
+        double t_best = 0.95 * t_none;
         for (int bin = kOrderBinsMax - 1; t_warm >= 0.0 && bin >= kSweepMinBin; --bin) {
             const int64_t nsw = hdeg2_sources_from_bin(g, bin);
             if (nsw == 0) continue;
@@ -336,7 +339,11 @@ extern "C" int kh_set_variant(kh_graph* G, int32_t op, int32_t variant, int32_t 
         if (variant != KH_VAR_AUTO && variant != KH_LEVELU_STEPPED && variant != KH_LEVELU_FREE &&
             variant != KH_LEVELU_GROUPED)
             return kh::set_error(g.ctx, KH_EINVAL, "unknown union schedule %d", variant);
+        if (slices < 0 || slices > 64 || (slices & (slices - 1)))
+            return kh::set_error(g.ctx, KH_EINVAL, "group divisor %d: 0 or a power of two up to 64",
+                                 slices);
         g.levelu_mode = variant;
+        g.levelu_div = slices;
         return KH_OK;
     }
     if (op == KH_OP_HDEG2_SWEEP) {
@@ -383,7 +390,7 @@ extern "C" int kh_get_variant(kh_graph* G, int32_t op, int32_t* variant, int32_t
     kh::Graph& g = G->g;
     if (op == KH_OP_PEEL_COMPACT || op == KH_OP_LEVEL_UNION) {
         if (variant) *variant = op == KH_OP_PEEL_COMPACT ? g.compact_mode : g.levelu_mode;
-        if (slices) *slices = 0;
+        if (slices) *slices = op == KH_OP_LEVEL_UNION ? g.levelu_div : 0;
         if (threads) *threads = 0;
         if (tuned_ms) *tuned_ms = 0.0;
         return KH_OK;

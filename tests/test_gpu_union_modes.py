@@ -1,6 +1,7 @@
-"""The three schedules of the level >= 2 union (Alg. 2 with Alg. 5's trim):
+"""The schedules of the level >= 2 union (Alg. 2 with Alg. 5's trim):
 barrier-separated steps, free-running warps, and free-running lane groups
-(fewer lanes per list as the lists outnumber the warps).  All must give the oracle's
+(sized by the keys a list is expected to give, or an eighth of them).  All
+must give the oracle's
 estimates (levels and |B|) and sampled cores bit for bit, including split hubs,
 small M (many trims and compactions) and refines that stop early."""
 import numpy as np
@@ -18,8 +19,8 @@ GRAPHS = {
     "hubs": lambda: gg.with_hubs(12000, (9000, 6000, 4500), 77),
     "rmat12": lambda: gg.rmat(12, 16, 0.57, 0.19, 0.19, 5),
 }
-MODES = {"stepped": K.KH_LEVELU_STEPPED, "free": K.KH_LEVELU_FREE,
-         "grouped": K.KH_LEVELU_GROUPED}
+MODES = {"stepped": (K.KH_LEVELU_STEPPED, 0), "free": (K.KH_LEVELU_FREE, 0),
+         "grouped": (K.KH_LEVELU_GROUPED, 0), "grouped8": (K.KH_LEVELU_GROUPED, 8)}
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +39,7 @@ def graph(ctx, name, h, M, mode):
     G = K.kh_graph_load_csr(ctx, rp, cl)
     K.kh_set_h(G, h)
     K.kh_set_sampling(G, seed=1, M=M)
-    K.kh_set_variant(G, MODES[mode], op=K.KH_OP_LEVEL_UNION)
+    K.kh_set_variant(G, MODES[mode][0], MODES[mode][1], op=K.KH_OP_LEVEL_UNION)
     return rp, cl, G
 
 
@@ -66,5 +67,21 @@ def test_cores_per_union_schedule(ctx, mode, name, h, M):
         core = K.kh_core_sampled(G)
         ro, rounds, _ = K.kh_peel_info(G)
         assert np.array_equal(core, want) and np.array_equal(ro, wround) and rounds == steps
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("mode", ["stepped", "grouped"])
+def test_largest_M_fits_and_matches(ctx, mode):
+    # M = 12000 (the library's largest): the hash set takes 2^15 slots and
+    # the kernel's shared memory must still fit; the 2-balls of the hubs of
+    # this graph exceed M, so the union trims and compacts
+    rp, cl, G = graph(ctx, "cl20k", 2, 12000, mode)
+    try:
+        want = O.estimate_dp(rp, cl, O.ranks(rp.size - 1, 1), 2, 12000)
+        got = K.kh_estimate(G)
+        for x, y in zip(got, want):
+            assert np.array_equal(x, y)
+        assert (want[1] > 0).any()  # some level above 0: the trim ran
     finally:
         G.close()
