@@ -673,7 +673,8 @@ int launch_hdeg(Graph& g, const int* worklist, const int* d_count, int64_t count
     if (cnt) kern = smem ? k_hdeg<true, true> : k_hdeg<true, false>;
     else kern = smem ? k_hdeg<false, true> : k_hdeg<false, false>;
     if (smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBitmapMax);
         if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_hdeg)");
     }
     int per_sm = 0;
@@ -833,7 +834,7 @@ extern "C" int kh_hdegree_exact_noalloc(int64_t n, const int64_t* rowptr, const 
     const int words = (int)((n + 31) / 32);
     const size_t dyn = (size_t)((((int64_t)words + 3) & ~(int64_t)3) * 4);
     void (*kern)(BfsArgs) = k_hdeg<false, true, true>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBitmapMax) !=
         cudaSuccess) {
         cudaGetLastError();
         return KH_ECUDA;

@@ -719,7 +719,7 @@ int run_sweeps(Graph& g, int32_t* deg, const int32_t* src, int64_t count, cudaSt
     const int use_filter = fsm <= (size_t)kSmem2Max ? 1 : 0;
     const size_t dyn = use_filter ? fsm : 0;
     KH_CUDA_TRY(g.ctx, cudaFuncSetAttribute(k_sweep_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(dyn > 0 ? dyn : 16)));
+                                            (int)kSmem2Max));
     int per_sm = 0;
     KH_CUDA_TRY(g.ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_count, 1024, dyn));
     if (per_sm < 1) return set_error(g.ctx, KH_EINVAL, "sweep kernel does not fit on an SM");
@@ -761,7 +761,8 @@ int launch_hdeg2_slice(Graph& g, int32_t* deg, int32_t* cnt, int jlo, int nj, cu
     const size_t dyn = hdeg2_smem(width);
     if (dyn > (size_t)kSmem2Max) return set_error(g.ctx, KH_EINVAL, "slice too wide for shared memory");
     void (*kern)(Slice2Args) = cnt ? k_hdeg2_slice<true> : k_hdeg2_slice<false>;
-    KH_CUDA_TRY(g.ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    KH_CUDA_TRY(g.ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kSmem2Max));
     int per_sm = 0;
     KH_CUDA_TRY(g.ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
     if (per_sm < 1) return set_error(g.ctx, KH_EINVAL, "slice kernel does not fit on an SM");

@@ -39,6 +39,12 @@ constexpr int64_t kSmemBitmapMax = 100 * 1024;
 
 // Dynamic shared memory the sliced 2-degree kernel may use per CTA (bytes).
 constexpr int64_t kSmem2Max = 220 * 1024;
+// Kernels whose dynamic shared memory depends on the graph set their
+// maximum-dynamic-shared-memory attribute to the largest size they can ever
+// use (a constant), not to the size of the launch at hand: contexts on other
+// host threads (the server's slots) launch the same kernels concurrently, and
+// a smaller value set by one between another's setting and its launch would
+// make that launch fail.
 
 // Error bits written by device-side checks.
 constexpr int kErrQueue = 1;   // BFS queue overflow

@@ -1610,7 +1610,10 @@ int launch_level(Graph& g, int level, const int* worklist, const int* d_count,
         g.levelu_mode == KH_LEVELU_STEPPED ? k_levelU<false> : k_levelU<true>;
     a.group_lists = g.levelu_mode == KH_LEVELU_FREE ? 0 : 1;
     a.group_div = g.levelu_div > 0 ? g.levelu_div : kGroupDivDefault;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    // the largest table any graph can ask for (M up to kMaxM)
+    const int lg_max = table_lg(kMaxM);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)levelU_smem(lg_max, levelU_stage_cap(lg_max, kMaxM)));
     if (e != cudaSuccess) return check_cuda(g.ctx, e, "cudaFuncSetAttribute(k_levelU)");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLuThreads, dyn);
