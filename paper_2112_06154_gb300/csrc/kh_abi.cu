@@ -109,6 +109,13 @@ static cudaEvent_t pool_event(Graph& g) {
 
 void prof_begin(Graph& g, int kind, cudaStream_t s) {
     if (!g.prof_on) return;
+    if (g.prof_ev->size() % 2 == 1) {
+        // a bracket left open (its launch returned an error before prof_end): drop it
+        g.ev_pool->push_back(g.prof_ev->back());
+        g.prof_ev->pop_back();
+        g.prof_kind->pop_back();
+        g.prof_snapi->pop_back();
+    }
     cudaEvent_t e = pool_event(g);
     if (!e) return;
     int64_t si = -1;
