@@ -1,23 +1,29 @@
 // kh_tune.cu -- the autotuner of the exact h-degree pass, and the dispatch of
 // the whole-graph exact h-degree / fixed-level count calls.
 //
-// Two kernels compute deg_2 of every node (Sec. 2) with different visited-set
+// Three kernels compute deg_2 of every node (Sec. 2) with different visited-set
 // layouts:
 //   KH_VAR_CTA     k_hdeg: one CTA per source, a visited bitmap of all n nodes
 //                  in shared memory (only while n bits fit), cleared per source;
 //   KH_VAR_SLICED  k_hdeg2_slice: (source, slice) items, a bitmap of one slice
-//                  of the id range, cleared through the words the item set.
+//                  of the id range, cleared through the words the item set;
+//   KH_VAR_SLICED_SMALL  the same for sources of large 2-hop work, and
+//                  k_hdeg2_small (a warp and a private hash set per source)
+//                  for the rest.
 // The sliced kernel has two launch parameters: the number of slices S (at
-// least what shared memory requires) and the CTA size.  The tuner times every
-// candidate on the same sample of sources (every k-th source of the
-// longest-first order, so every size class is represented) with CUDA events on
-// the context stream, keeps the fastest for the graph, and records it in a
-// choice table keyed by the graph's shape class (device SMs, log2 n, log2 nnz,
-// log2 of max degree / mean degree).  With the environment variable
-// KH_TUNE_FILE set, the table is read from and appended to that text file, so
-// a later process on a graph of the same class skips the measurement.
-// The choice changes the schedule only: every candidate computes the same
-// degrees.
+// least what shared memory requires) and the CTA size.  With a sliced layout
+// the sources of the largest 2-hop work may go to the bit-parallel sweeps
+// (k_sweep_*: 128 sources per pass over the rows), from a work threshold.
+// The tuner times every layout candidate on the same sample of sources (every
+// k-th source of the longest-first order, so every size class is represented)
+// with CUDA events on the context stream, keeps the fastest, then prices the
+// sweep thresholds (sweeps times a measured sweep, plus the sliced layout on
+// the rest of the sample), and records the choice in a table keyed by the
+// graph's shape class (device SMs, log2 n, log2 nnz, log2 of max degree / mean
+// degree).  With the environment variable KH_TUNE_FILE set, the table is read
+// from and appended to that text file, so a later process on a graph of the
+// same class skips the measurement.  The choice changes the schedule only:
+// every candidate computes the same degrees.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
