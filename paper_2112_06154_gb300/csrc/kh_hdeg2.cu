@@ -18,6 +18,11 @@
 //
 // The bitmap is cleared between items through the list of words the item set
 // first (when it fits), otherwise with vector stores over the whole slice.
+//
+// Two more kernels serve the same pass: sources of small 2-hop work on one
+// warp each with a private hash set (k_hdeg2_small), and, for the sources of
+// the largest 2-hop work, bit-parallel sweeps of 128 sources at a time
+// (k_sweep_*; see the comment above them).
 #include <vector>
 
 #include "kh_internal.cuh"
