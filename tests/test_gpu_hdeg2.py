@@ -92,7 +92,7 @@ SWEEP_GRAPHS = {
     "ragged": _ragged,
     "cl20k": lambda: gg.chung_lu(20000, 20, 2.5, 1500, 1102),
     "rmat14": lambda: gg.rmat(14, 16, 0.57, 0.19, 0.19, 7),
-    # rows longer than the sweep kernel's head of 512 entries: one tail piece
+    # rows longer than the sweep kernel's head of 64 entries: one tail piece
     # (a star of 1500 leaves), several pieces (hubs of 9000 / 6000 / 4500)
     "star1500": lambda: gg.star(1500),
     "hubs": lambda: gg.with_hubs(12000, (9000, 6000, 4500), 77),
