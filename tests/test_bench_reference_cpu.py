@@ -24,3 +24,22 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_table_lines(tmp_path, monkeypatch):
+    import bench
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic_per_launch.txt").write_text(
+        "# comment\nwl_a levelU ratio 0.5\nwl_a bfs 1234.5\nwl_b levelU 99\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_traffic("wl_a", "levelU", 1000.0) == 500.0  # ratio x algorithmic bytes
+    assert bench.profile_traffic("wl_a", "bfs", 1000.0) == 1234.5    # bytes per launch
+    assert bench.profile_traffic("wl_b", "levelU", 1000.0) == 99.0
+    assert bench.profile_traffic("wl_a", "peel", 1000.0) is None
+
+
+def test_committed_traffic_line_is_the_levelU_ratio():
+    import bench
+    wl = bench.Workload("rmat")
+    assert bench.profile_traffic(wl.name, "levelU", 1e8) == 0.52 * 1e8
